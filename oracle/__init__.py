@@ -1,0 +1,15 @@
+"""CPU oracle for the Newton-Schulz polar factorisation (arXiv 2112.09017, Sec. III.D).
+
+TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check in
+``__graft_entry__.smoke`` and the CPU-baseline leg of ``bench.py`` may import
+anything from here. The CUDA library never does, and shares no code with it.
+
+Modules:
+  ns_polar    float64 Newton-Schulz polar factorisation, Frobenius scaling,
+              residual stop rule, H = sym(U^T A), and the error metrics
+  scalar      the scalar recurrences (Eqs. NS_scalar, a_def, RogueScalar) and
+              the exact-arithmetic residual trajectory predicted from a spectrum
+  jacobi_svd  one-sided Jacobi SVD, the independent checker on small inputs
+  precision   bit-level BF16 plane split and an emulator of split products
+"""
+from . import jacobi_svd, ns_polar, precision, scalar  # noqa: F401

@@ -1,0 +1,85 @@
+"""Bit-level definition of the BF16 plane split, and an emulator of
+split-precision products, in numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring of ``oracle``).
+
+The paper runs its FP32 products on BF16 multipliers with FP32 accumulation
+through an unspecified multi-pass scheme (Sec. II). The reading taken here:
+an FP32 value x is written as a sum of P BF16 "planes", each the
+round-to-nearest-even BF16 value of what the previous planes left over:
+
+  x_0 = bf16_rne(x),  x_1 = bf16_rne(x - x_0),  x_2 = bf16_rne(x - x_0 - x_1).
+
+For normal FP32 x the differences are exact in FP32 (each plane is within a
+factor of two of what it rounds), and with P = 3 the planes sum back to x
+exactly (8 + 8 + 8 significand bits cover FP32's 24).
+
+A split product keeps the plane pairs (p, q) with p + q < P, plus (1, 1) when
+P = 3, i.e. every term down to relative size 2^-16:
+  P = 1: (0,0)                              1 pass  ("bf16")
+  P = 2: (0,0) (0,1) (1,0)                  3 passes ("bf16x3")
+  P = 3: (0,0) (0,1) (1,0) (0,2) (2,0) (1,1) 6 passes ("bf16x6")
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["bf16_rne_bits", "bf16_rne", "split_planes", "plane_pairs", "emulated_matmul",
+           "bits_to_float"]
+
+PAIRS = {
+    1: ((0, 0),),
+    2: ((0, 0), (0, 1), (1, 0)),
+    3: ((0, 0), (0, 1), (1, 0), (0, 2), (2, 0), (1, 1)),
+}
+
+
+def plane_pairs(p: int):
+    return PAIRS[p]
+
+
+def bf16_rne_bits(x) -> np.ndarray:
+    """Round float32 values to BF16 with round-to-nearest-even; return the
+    16-bit patterns (uint16). NaN stays NaN (quiet bit set)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = x.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) & 0xFFFF
+    nan = np.isnan(x)
+    if np.any(nan):
+        r = np.where(nan, ((u >> 16) | 0x0040) & 0xFFFF, r)
+    return r.astype(np.uint16)
+
+
+def bits_to_float(b) -> np.ndarray:
+    """BF16 bit patterns (uint16) to the float32 values they encode."""
+    b = np.asarray(b, dtype=np.uint16)
+    return (b.astype(np.uint32) << 16).view(np.float32)
+
+
+def bf16_rne(x) -> np.ndarray:
+    """float32 -> nearest-even BF16 value, returned as float32."""
+    return bits_to_float(bf16_rne_bits(x))
+
+
+def split_planes(x, p: int):
+    """Split float32 x into p BF16 planes; returns a list of uint16 arrays."""
+    rem = np.asarray(x, dtype=np.float32)
+    planes = []
+    for _ in range(p):
+        b = bf16_rne_bits(rem)
+        planes.append(b)
+        rem = (rem - bits_to_float(b)).astype(np.float32)
+    return planes
+
+
+def emulated_matmul(a, b, p: int) -> np.ndarray:
+    """Model of a P-plane split product op(A) @ op(B): every product input
+    rounded to its BF16 plane, float32 accumulation (numpy sgemm) per pass,
+    passes summed in float32 in the order of ``plane_pairs``."""
+    ap = [bits_to_float(q) for q in split_planes(a, p)]
+    bp = [bits_to_float(q) for q in split_planes(b, p)]
+    acc = np.zeros((a.shape[0], b.shape[1]), dtype=np.float32)
+    for i, j in plane_pairs(p):
+        acc += ap[i] @ bp[j]
+    return acc

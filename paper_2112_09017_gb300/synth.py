@@ -1,0 +1,142 @@
+"""Seeded synthetic inputs with prescribed singular spectra.
+
+This module is shared by the CUDA path's tests/bench and by the CPU oracle's
+tests. It holds no arithmetic of the polar method itself: it only draws
+matrices A = fl32(Q1 diag(sigma) Q2^T) whose singular values sigma are fixed
+in advance, so that the exact polar factor U = Q1 Q2^T and H = Q2 diag(sigma)
+Q2^T are known in closed form (Sec. III.D, Eq. SVDdef).
+
+Recipe (every step seeded, numpy PCG64 through ``default_rng(seed)``):
+
+* Q1 (m x n, orthonormal columns) and then Q2 (n x n) are the Householder-QR
+  Q factors of standard-Gaussian matrices drawn in that order, with the sign of
+  each column fixed so that diag(R) > 0 (the Haar-distributed choice).
+* sigma is log-spaced, largest first, on [sigma_min, 1]; the two-segment
+  variant puts 90% of the values on [1e-3, 1] and the rest on [1e-8, 1e-3].
+* A is formed in float64 and rounded once to float32 (row-major, C order).
+
+Batched problems draw their own (m, n) and matrices from ``default_rng(i)``
+for problem index i.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "haar_columns", "logspace_spectrum", "two_segment_spectrum", "matrix_with_spectrum",
+    "Workload", "WORKLOADS", "make_workload", "batched_sizes", "batched_problem",
+]
+
+
+def haar_columns(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    """rows x cols float64 matrix with orthonormal columns (rows >= cols)."""
+    g = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(g, mode="reduced")
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    return q * d[None, :]
+
+
+def logspace_spectrum(n: int, sigma_min: float, sigma_max: float = 1.0) -> np.ndarray:
+    """n singular values log-spaced from sigma_max down to sigma_min."""
+    if n == 1:
+        return np.array([sigma_max], dtype=np.float64)
+    return np.logspace(math.log10(sigma_max), math.log10(sigma_min), n)
+
+
+def two_segment_spectrum(n: int) -> np.ndarray:
+    """90% of the values log-spaced on [1e-3, 1], the rest on [1e-8, 1e-3]."""
+    n_hi = int(math.floor(0.9 * n))
+    hi = logspace_spectrum(n_hi, 1e-3, 1.0)
+    lo = logspace_spectrum(n - n_hi, 1e-8, 1e-3) if n > n_hi else np.zeros(0)
+    return np.concatenate([hi, lo])
+
+
+def matrix_with_spectrum(m: int, n: int, sigma: np.ndarray, seed: int,
+                         return_factors: bool = False):
+    """A = fl32(Q1 diag(sigma) Q2^T) with Q1, Q2 drawn from default_rng(seed).
+
+    Returns the float32 C-contiguous m x n matrix, and with
+    ``return_factors`` also (Q1, sigma, Q2) in float64.
+    """
+    if m < n:
+        raise ValueError("m >= n required")
+    sigma = np.asarray(sigma, dtype=np.float64)
+    if sigma.shape != (n,):
+        raise ValueError("sigma must have n entries")
+    rng = np.random.default_rng(seed)
+    q1 = haar_columns(rng, m, n)
+    q2 = haar_columns(rng, n, n)
+    a64 = (q1 * sigma[None, :]) @ q2.T
+    a32 = np.ascontiguousarray(a64.astype(np.float32))
+    if return_factors:
+        return a32, (q1, sigma, q2)
+    return a32
+
+
+@dataclass(frozen=True)
+class Workload:
+    """A single-solve workload: shape, spectrum recipe, seed and stop tolerance."""
+    name: str
+    m: int
+    n: int
+    sigma_min: float        # smallest singular value (log-spaced spectrum), or 0 for two-segment
+    seed: int = 0
+    tol: float = 1e-6
+
+    @property
+    def kappa(self) -> float:
+        return 1e8 if self.sigma_min == 0.0 else 1.0 / self.sigma_min
+
+    def spectrum(self) -> np.ndarray:
+        if self.sigma_min == 0.0:
+            return two_segment_spectrum(self.n)
+        return logspace_spectrum(self.n, self.sigma_min)
+
+    def matrix(self, return_factors: bool = False):
+        return matrix_with_spectrum(self.m, self.n, self.spectrum(), self.seed, return_factors)
+
+
+# The five benchmark workloads (square 512 plain-FP32 case, square 8192, tall
+# 32768x8192, batched uneven, square 32768 two-segment spectrum).
+WORKLOADS = {
+    "square512_k1e2": Workload("square512_k1e2", 512, 512, 1e-2),
+    "square8192_k1e4": Workload("square8192_k1e4", 8192, 8192, 1e-4),
+    "tall32768x8192_k1e6": Workload("tall32768x8192_k1e6", 32768, 8192, 1e-6),
+    "square32768_k1e8": Workload("square32768_k1e8", 32768, 32768, 0.0),
+}
+
+
+def make_workload(name: str, return_factors: bool = False):
+    return WORKLOADS[name].matrix(return_factors)
+
+
+def batched_sizes(count: int, n_lo: int = 64, n_hi: int = 1024):
+    """(m, n) of batched problem i for i < count: n uniform on [n_lo, n_hi],
+    m = n or 2n with probability 1/2, both drawn from default_rng(i)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(i)
+        n = int(rng.integers(n_lo, n_hi + 1))
+        m = n if rng.random() < 0.5 else 2 * n
+        out.append((m, n))
+    return out
+
+
+def batched_problem(i: int, sigma_min: float = 1e-3, n_lo: int = 64, n_hi: int = 1024,
+                    return_factors: bool = False):
+    """Batched problem i: its size from ``batched_sizes`` and its matrix drawn
+    from default_rng(i) after the size draws."""
+    rng = np.random.default_rng(i)
+    n = int(rng.integers(n_lo, n_hi + 1))
+    m = n if rng.random() < 0.5 else 2 * n
+    sigma = logspace_spectrum(n, sigma_min)
+    q1 = haar_columns(rng, m, n)
+    q2 = haar_columns(rng, n, n)
+    a32 = np.ascontiguousarray(((q1 * sigma[None, :]) @ q2.T).astype(np.float32))
+    if return_factors:
+        return a32, (q1, sigma, q2)
+    return a32
