@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the Newton-Schulz polar factorisation A = U H on GB300.
+
+One step = one whole polar solve (||A||_F, X_0 = A/||A||_F, the Newton-Schulz loop
+to ||X^T X - I||_F / sqrt(n) <= tol, U and H = sym(U^T A)) of a seeded synthetic
+matrix with a prescribed spectrum, input resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload square8192_k1e4] [--prec bf16x6] [--no-plain] [--no-cpu]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
+problem of the same size (independent replicas; the single solve does not shard),
+so `value` is the whole-job throughput and scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "polar TFLOP/s & solves/s at ≤5e-6 orth error: mixed vs plain FP32, one GB300"
+DEFAULT_WORKLOAD = "square8192_k1e4"
+
+
+def algorithmic_flops(m, n, iters):
+    """(iters + 1) Grams of m n^2 (symmetric half), iters updates of 2 m n^2, and
+    U^T A for H (2 m n^2): m n^2 (3 iters + 3)."""
+    return float(m) * n * n * (3 * iters + 3)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                mhz.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def accuracy(torch, A, U, H, q1q2t=None):
+    """orth, bwd (and fwd against the closed-form U = Q1 Q2^T when given), in float64 on the GPU."""
+    A64, U64, H64 = A.double(), U.double(), H.double()
+    n = U.shape[1]
+    orth = (torch.linalg.matrix_norm(U64.T @ U64 - torch.eye(n, dtype=torch.float64, device=U.device)) /
+            math.sqrt(n)).item()
+    bwd = (torch.linalg.matrix_norm(A64 - U64 @ H64) / torch.linalg.matrix_norm(A64)).item()
+    out = {"orth": orth, "bwd": bwd}
+    if q1q2t is not None:
+        out["fwd_closed_form"] = (torch.linalg.matrix_norm(U64 - q1q2t) / math.sqrt(n)).item()
+    return out
+
+
+def cpu_oracle_sample(a_np, tol, max_iter=1):
+    """The oracle as it stands on a bounded sample: a whole oracle solve truncated to
+    max_iter updates (max_iter + 1 Grams, max_iter updates, H)."""
+    from oracle.ns_polar import ns_polar
+    m, n = a_np.shape
+    t0 = time.perf_counter()
+    out = ns_polar(a_np, tol=tol, max_iter=max_iter)
+    dt = time.perf_counter() - t0
+    flops = algorithmic_flops(m, n, out["iters"])
+    return flops, dt, out["iters"]
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed as it stands on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2112_09017_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    a = w.matrix()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(a, w.tol)
+    tot_f, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        f, t, _ = cpu_oracle_sample(a, w.tol)
+        tot_f += f
+        tot_t += t
+    value = tot_f / tot_t / 1e12
+    cores = cpu_cores()
+    sample = (f"oracle ns_polar (numpy float64) truncated to 1 Newton-Schulz update per step (2 Grams, 1 update, "
+              f"H) on the full {w.m}x{w.n} matrix; rate = algorithmic flops m n^2 (3k+3) / wall time")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "kappa": w.kappa, "tol": w.tol},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    from paper_2112_09017_gb300 import build, synth
+    build.ensure_built()
+    from paper_2112_09017_gb300 import polar
+    lib = polar
+    w = synth.WORKLOADS[args.workload]
+    m, n = w.m, w.n
+    a_np, (q1, s, q2) = synth.matrix_with_spectrum(m, n, w.spectrum(), w.seed + rank, return_factors=True)
+    A = torch.from_numpy(a_np).cuda()
+    U = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    H = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = load_peaks()
+
+    def timed(plan, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            plan(A, U=U, H=H)
+        barrier(world)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        ev0.record(stream)
+        for _ in range(steps):
+            _, _, info = plan(A, U=U, H=H)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1)
+        return max_over_ranks(ms, world), infos, clocks
+
+    # ---- mixed / split precision (the chosen form) ----
+    plan = lib.Plan(m, n, prec=args.prec, tol=w.tol, profile=1)
+    sampler = ClockSampler(local)
+    ms, infos, clocks = timed(plan, args.steps, args.warmup, sampler)
+    iters = infos[-1]["iters"]
+    flops = sum(algorithmic_flops(m, n, i["iters"]) for i in infos)
+    value = world * flops / (ms * 1e-3) / 1e12
+    solves_per_s = world * args.steps / (ms * 1e-3)
+    acc = accuracy(torch, A, U, H, torch.from_numpy(q1 @ q2.T).cuda() if rank == 0 else None)
+
+    # dominant kernel: the update product X <- 1.5 X - 0.5 X G (2/3 of the flops)
+    P = {"bf16x6": 3, "bf16x3": 2, "bf16": 1, "fp32": 0}.get(args.prec, 3)
+    n_upd = sum(i["n_update"] for i in infos)
+    ms_upd = sum(i["ms_update"] for i in infos)
+    n_gram = sum(i["n_gram"] for i in infos)
+    ms_gram = sum(i["ms_gram"] for i in infos)
+    roofline = None
+    if n_upd > 0 and ms_upd > 0:
+        avg_s = ms_upd / n_upd * 1e-3
+        if P > 0:
+            work = lib.PASSES[P] * 2.0 * m * n * n      # BF16 MMA flops the split product issues
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            ach = work / avg_s / 1e12
+            roofline = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "traffic": None, "kernel": "update product (tcgen05, split BF16)",
+                        "peak_source": f"{peak_src} bf16 sustained", "launch_ms": avg_s * 1e3}
+        else:
+            work = 2.0 * m * n * n
+            mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            sms = lib.polar_device_query()[0]
+            peak = sms * 128 * 2 * mhz * 1e6 / 1e12    # FP32 FFMA lanes x 2 flops x clock
+            ach = work / avg_s / 1e12
+            roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": None, "kernel": "update product (SIMT FP32)",
+                        "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz", "launch_ms": avg_s * 1e3}
+    launches = sum(i["launches"] for i in infos)
+
+    # ---- end to end through the C ABI with host buffers ----
+    A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+    A_h.copy_(torch.from_numpy(a_np))
+    U_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+    H_h = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+    A_d = torch.empty_like(A)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    e2e_flops = 0.0
+    for _ in range(e2e_steps):
+        A_d.copy_(A_h, non_blocking=True)
+        _, _, info = plan(A_d, U=U, H=H)
+        U_h.copy_(U, non_blocking=True)
+        H_h.copy_(H, non_blocking=True)
+        e2e_flops += algorithmic_flops(m, n, info["iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    e2e = {"value": world * e2e_flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": (m * n + n * n) * 4,
+           "ms_per_step": e2e_ms / e2e_steps}
+    plan.close()
+
+    # ---- the plain FP32 form on the same input ----
+    plain = None
+    if not args.no_plain and args.prec != "fp32":
+        pplan = lib.Plan(m, n, prec="fp32", tol=w.tol)
+        pms, pinfos, _ = timed(pplan, max(1, min(args.steps, 3)), min(args.warmup, 3))
+        pflops = sum(algorithmic_flops(m, n, i["iters"]) for i in pinfos)
+        pacc = accuracy(torch, A, U, H)
+        plain = {"value": world * pflops / (pms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "ms_per_step": pms / len(pinfos), "iters": pinfos[-1]["iters"], **pacc}
+        pplan.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
+    cpu = None
+    if not args.no_cpu and world == 1:
+        f, t, it = cpu_oracle_sample(a_np, w.tol, max_iter=1)
+        cpu = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"oracle ns_polar (numpy float64) on the full {m}x{n} matrix truncated to {it} update "
+                         f"({it + 1} Grams, {it} update, H): {t:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16x6": "bf16x6 split, f32 accumulate", "bf16x3": "bf16x3 split, f32 "
+                                           "accumulate", "bf16": "bf16, f32 accumulate", "fp32": "f32"}.get(
+                args.prec, args.prec),
+            "data": "synthetic",
+            "config": {"workload": w.name, "m": m, "n": n, "kappa": w.kappa, "tol": w.tol, "precision": args.prec,
+                       "l2": f"inputs larger than L2 (A is {m * n * 4 / 2**20:.0f} MiB; L2 129 MB)",
+                       "parallelism": "independent replicas" if world > 1 else "single GPU"},
+            "solves_per_s": solves_per_s, "iters": iters,
+            "paper_convention_tflops": value * (4.0 * iters) / (3 * iters + 3),
+            "accuracy": acc,
+            "kernel_ms": {"gram_avg": ms_gram / max(n_gram, 1), "update_avg": ms_upd / max(n_upd, 1),
+                          "n_gram": n_gram, "n_update": n_upd},
+            "plain_fp32": plain,
+            "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--prec", default="bf16x6")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * polar.h - C ABI of the GB300 Newton-Schulz polar factorisation library (libpolar.so).
+ *
+ * The method (arXiv 2112.09017, Sec. III.D): the polar decomposition A = U H of an
+ * m x n matrix A, m >= n (Eq. PolarDecomp), with U having orthonormal columns and H
+ * symmetric positive semi-definite, is the fixed point of the Newton-Schulz iteration
+ * X_{k+1} = X_k (3 I - X_k^T X_k) / 2 (Eq. NewtonSchulz) started from the Frobenius-
+ * scaled X_0 = A / ||A||_F (Sec. III.D and the first step of Algorithm 1). This library
+ * runs that iteration until ||X_k^T X_k - I||_F / sqrt(n) <= tol and returns U = X_k and
+ * H = (U^T A + A^T U) / 2 (Algorithm 1, "Ensure": H = U^H A).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are row-major float32. Element (i, j) of a matrix with leading dimension ld
+ *    is at p[i * ld + j]; ld >= number of columns.
+ *  - Matrix pointers are DEVICE pointers (cudaMalloc'd or equivalent) unless stated.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *  - `stream` is a cudaStream_t cast to void* (NULL = the legacy default stream).
+ *  - Entry points return a polar_status_t and never abort, exit or trap. Invalid
+ *    arguments are rejected before any device work with POLAR_EINVAL.
+ *  - The library has no CPU fallback: without a usable sm_103 device every call that
+ *    needs one returns POLAR_ECUDA.
+ *  - A plan may be used by one host thread / one stream at a time.
+ */
+#ifndef POLAR_H
+#define POLAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POLAR_API __attribute__((visibility("default")))
+#else
+#define POLAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  POLAR_OK = 0,
+  POLAR_NOT_CONVERGED = 1,  /* stopped by stagnation or max_iter; U, H of the last iterate returned */
+  POLAR_EINVAL = -1,        /* bad argument: null pointer, m < n, n < 1, ld too small, aliasing */
+  POLAR_ENOMEM = -2,        /* device allocation failed or workspace above ws_limit */
+  POLAR_ECUDA = -3,         /* CUDA runtime/driver error, or no sm_103 device */
+  POLAR_ENONFINITE = -4,    /* ||A||_F is zero, Inf or NaN, or a residual became non-finite */
+  POLAR_ETIMEOUT = -5,      /* a bounded device-side wait expired (kernel returned early) */
+  POLAR_ENOTSUP = -6        /* precision mode or shape not supported by this build */
+} polar_status_t;
+
+/* How the matrix products of the iteration are computed.
+ *   FP32      every product in float32 FFMA on the SIMT cores (the plain form)
+ *   BF16X6    float32 operands split into 3 BF16 planes, 6 tensor-core passes
+ *             (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid), float32 accumulation
+ *   BF16X3    2 BF16 planes, 3 passes (hi*hi, hi*lo, lo*hi)
+ *   BF16      1 BF16 plane, 1 pass
+ *   SCHED_BF16_THEN_X3   BF16 while the residual is above switch_residual, then BF16X3
+ *   AUTO      BF16X6 for n >= 256, FP32 below
+ * TF32X3 and SCHED_FP8_BF16_X3 are reserved (POLAR_ENOTSUP in this build). */
+typedef enum {
+  POLAR_FP32 = 0,
+  POLAR_BF16X6 = 1,
+  POLAR_TF32X3 = 2,
+  POLAR_BF16X3 = 3,
+  POLAR_SCHED_BF16_THEN_X3 = 4,
+  POLAR_SCHED_FP8_BF16_X3 = 5,
+  POLAR_AUTO = 6,
+  POLAR_BF16 = 7
+} polar_precision_t;
+
+typedef void* polar_stream_t;
+typedef struct polar_plan_s* polar_plan_t;
+
+typedef struct {
+  double tol;              /* stop when ||X^T X - I||_F / sqrt(n) <= tol; <= 0 means 1e-6 */
+  int max_iter;            /* maximum number of updates; <= 0 means 100 */
+  int prec;                /* a polar_precision_t */
+  double stagnation;       /* stop (NOT_CONVERGED) when r_k > stagnation * r_{k-2} ... ; <= 0 means 0.7 */
+  double stag_floor;       /* ... and r_k < stag_floor; <= 0 means 1e-4 */
+  double switch_residual;  /* schedules: residual below which the finer precision is used; <= 0 means 1e-2 */
+  size_t ws_limit;         /* maximum workspace bytes a plan may allocate; 0 = no limit */
+  int profile;             /* nonzero: time every Gram and update launch with CUDA events (info) */
+} polar_options_t;
+
+#define POLAR_HIST 128
+
+typedef struct {
+  int status;                 /* the polar_status_t of the run */
+  int iters;                  /* Newton-Schulz updates applied (U = X_iters) */
+  int prec;                   /* precision mode used */
+  int hist_len;               /* number of valid entries in res_hist / planes_hist */
+  double residual;            /* ||U^T U - I||_F / sqrt(n) as measured at the returned U (float32 Gram) */
+  double normA_F;             /* ||A||_F (float64 accumulation) */
+  double sym_err;             /* ||skew(U^T A)||_F / ||U^T A||_F */
+  float ms_total;             /* device time of the whole solve (CUDA events), milliseconds */
+  int launches;               /* kernels this run enqueued (including ones that found the run stopped) */
+  int n_gram, n_update;       /* profile: Gram and update launches that did work */
+  float ms_gram, ms_update;   /* profile: their summed device time (CUDA events), milliseconds */
+  double res_hist[POLAR_HIST];         /* r_k for k = 0 .. hist_len-1 */
+  unsigned char planes_hist[POLAR_HIST];/* BF16 planes of the Gram at step k (0 = FP32 SIMT) */
+} polar_info_t;
+
+/* Fill *o with the defaults listed in polar_options_t (prec = POLAR_BF16X6). */
+POLAR_API void polar_default_options(polar_options_t* o);
+
+/* Human-readable name of a status code (static string). */
+POLAR_API const char* polar_status_string(polar_status_t s);
+
+/* Create a plan for m x n problems (m >= n >= 1) and allocate its device workspace
+ * on the current CUDA device. o may be NULL for defaults. The plan owns the workspace
+ * until polar_plan_destroy. Errors: EINVAL (shape, prec), ENOMEM (allocation or
+ * ws_limit), ENOTSUP (reserved prec), ECUDA. */
+POLAR_API polar_status_t polar_plan_create(polar_plan_t* plan, int64_t m, int64_t n, const polar_options_t* o);
+
+/* Bytes of device workspace the plan holds. */
+POLAR_API size_t polar_plan_workspace_bytes(polar_plan_t plan);
+
+/* Polar factorisation of A (m x n, lda >= n), writing U (m x n, ldu >= n) and
+ * H (n x n, ldh >= n). tol <= 0 uses the plan's tolerance. A is read-only; U and H
+ * must not overlap A or each other (EINVAL). Work is enqueued on `stream`; the call
+ * returns after the solve has finished and *info (may be NULL) is filled.
+ * Returns OK, NOT_CONVERGED (U, H of the last iterate are still written),
+ * ENONFINITE (U and H untouched), ETIMEOUT or ECUDA.
+ * Paper: Sec. III.D, Eqs. NewtonSchulz and PolarDecomp, Algorithm 1. */
+POLAR_API polar_status_t polar_run(polar_plan_t plan, const float* A, int64_t lda, float* U, int64_t ldu,
+                         float* H, int64_t ldh, double tol, polar_info_t* info, polar_stream_t stream);
+
+/* Plan for `count` independent problems of sizes (m[i], n[i]) (host arrays), m[i] >= n[i] >= 1.
+ * Problem i's matrices are packed row-major (ld = n[i]). */
+POLAR_API polar_status_t polar_batched_plan_create(polar_plan_t* plan, int count, const int64_t* m,
+                                         const int64_t* n, const polar_options_t* o);
+
+/* Polar factorisation of every problem of a batched plan. A, U, H are HOST arrays of
+ * `count` DEVICE pointers (A[i]: m_i x n_i, U[i]: m_i x n_i, H[i]: n_i x n_i, all packed).
+ * iters_dev[i] (int32) and resid_dev[i] (float64) are device arrays receiving each
+ * problem's update count and final residual; either may be NULL. Stream-asynchronous:
+ * returns after enqueueing; per-problem status goes to the device arrays (a problem
+ * that did not converge reports iters = -1 - updates). */
+POLAR_API polar_status_t polar_batched_run(polar_plan_t plan, const float* const* A, float* const* U,
+                                 float* const* H, double tol, int32_t* iters_dev, double* resid_dev,
+                                 polar_stream_t stream);
+
+POLAR_API void polar_plan_destroy(polar_plan_t plan);
+
+/* C = alpha * op(A) op(B) + beta * C, op(X) = X or X^T (trans != 0), with op(A) M x K and
+ * op(B) K x N, in precision `prec` (FP32, BF16, BF16X3, BF16X6). beta == 0 does not read C.
+ * Stream-asynchronous. Split planes live in a library-owned per-device scratch buffer
+ * that grows on demand (so this call may allocate). The building block of every step
+ * of the iteration (Eq. NewtonSchulz is two such products). */
+POLAR_API polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                          const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                          float* C, int64_t ldc, int prec, polar_stream_t stream);
+
+/* C = alpha * A^T A + beta * C for A k x n (lda >= n), C n x n (ldc >= n), storing the full
+ * symmetric C (each off-diagonal pair computed once and mirrored). The Gram matrix
+ * X^T X of Eq. NewtonSchulz. Stream-asynchronous; may allocate scratch as polar_gemm. */
+POLAR_API polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int64_t lda, float beta,
+                          float* C, int64_t ldc, int prec, polar_stream_t stream);
+
+/* Split `count` float32 values into `planes` (1..3) BF16 planes with round-to-nearest-even
+ * on each remainder: out[p * count + i] holds plane p of X[i] as a BF16 bit pattern.
+ * X and out are device pointers. The operand encoding of the split-precision products
+ * (Sec. II: FP32 products emulated on BF16 multipliers). Stream-asynchronous. */
+POLAR_API polar_status_t polar_split_bf16(const float* X, int64_t count, int planes, uint16_t* out,
+                                polar_stream_t stream);
+
+/* Number of SMs and compute capability of the current device; ECUDA without one. */
+POLAR_API polar_status_t polar_device_query(int* sm_count, int* cc_major, int* cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLAR_H */

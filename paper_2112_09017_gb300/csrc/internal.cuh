@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of libpolar.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/polar.h"
+
+namespace polar {
+
+// Iteration state kept in device memory by a single-solve plan.
+// Status values written by device code.
+enum : int {
+  ST_RUNNING = 0,
+  ST_CONVERGED = 1,
+  ST_NOT_CONVERGED = 2,
+  ST_NONFINITE = 3,
+  ST_TIMEOUT = 4,
+};
+
+struct DevState {
+  double normA;          // ||A||_F
+  double inv_sqrt_n;     // 1 / sqrt(n)
+  int status;            // ST_*
+  int iters;             // updates applied so far (the U = X_iters iterate)
+  int planes_next;       // planes of the next product (schedules)
+  int hist_len;
+  unsigned int err_flags;// device error bits (timeouts)
+  int pad;
+  double ring[4];        // r_k at slot k % 4 (stagnation test beyond the history)
+  double sym_err;        // ||skew(U^T A)||_F / ||U^T A||_F
+  double res_hist[POLAR_HIST];
+  unsigned char planes_hist[POLAR_HIST];
+};
+
+// Parameters of the stop rule evaluated on the device after every Gram.
+struct StopRule {
+  double tol;
+  double stagnation;
+  double stag_floor;
+  double switch_residual;
+  int max_iter;
+  int sched;      // 0: fixed planes, 1: BF16 then BF16X3
+  int planes_fixed;
+};
+
+// ---------------------------------------------------------------------------------
+// Misc kernels (kernels_misc.cu)
+// Frobenius norm: per-block float64 partials, then a fixed-order final sum.
+int frob_partials_blocks(int64_t m, int64_t n);
+cudaError_t launch_frob_partials(const float* A, int64_t m, int64_t n, int64_t lda, double* partials,
+                                 int blocks, cudaStream_t s);
+cudaError_t launch_norm_finalize(const double* partials, int nparts, DevState* st, double inv_sqrt_n,
+                                 int planes_first, cudaStream_t s);
+// dst = src / ||A||_F (if scale) or src (otherwise); optional float32 copy and BF16 planes.
+cudaError_t launch_scale_split(const float* src, int64_t lds, int64_t m, int64_t n, const DevState* st,
+                               bool scale, float* dst, int64_t ldd, uint16_t* planes, int64_t ldp,
+                               int64_t plane_stride, int nplanes, cudaStream_t s);
+// Residual finalize: fixed-order sum of Gram partials, stop rule, schedule.
+cudaError_t launch_residual_finalize(const double* partials, int nparts, DevState* st, StopRule rule,
+                                     int k, int planes_this, cudaStream_t s);
+// H = (C + C^T)/2 from C = U^T A (n x n, ldc), and partials of ||skew C||^2, ||C||^2.
+cudaError_t launch_symmetrize(const float* C, int64_t ldc, int64_t n, float* H, int64_t ldh,
+                              double* partials, int blocks, cudaStream_t s);
+int symmetrize_blocks(int64_t n);
+cudaError_t launch_sym_finalize(const double* partials, int blocks, DevState* st, cudaStream_t s);
+// C[j][i] = C[i][j] for every i < j (n x n float32), or the same on `nplanes` BF16 planes.
+cudaError_t launch_mirror_f32(float* C, int64_t ldc, int64_t n, const DevState* st, cudaStream_t s);
+cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride, int nplanes, int64_t n,
+                                 const DevState* st, const int* planes_dyn, cudaStream_t s);
+cudaError_t launch_copy2d(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t m, int64_t n,
+                          cudaStream_t s);
+cudaError_t launch_split_flat(const float* x, int64_t count, int nplanes, uint16_t* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// SIMT float32 GEMM / SYRK (gemm_simt.cu)
+enum SimtEpi : int { SIMT_EPI_STORE = 0, SIMT_EPI_NS = 1, SIMT_EPI_GRAM = 2 };
+
+struct SimtArgs {
+  int64_t M, N, K;
+  const float* A; int64_t lda; int a_kmajor;   // a_kmajor: A stored M x K (row-major); else K x M
+  const float* B; int64_t ldb; int b_kmajor;   // b_kmajor: B stored N x K; else K x N
+  float* C; int64_t ldc;
+  float alpha, beta;
+  const float* Xold; int64_t ldx;              // NS epilogue: C = 1.5 Xold - 0.5 acc
+  double* partials;                            // GRAM epilogue: one float64 per tile
+  const DevState* st;                          // skip if st && st->status != RUNNING
+  int triangular;                              // SYRK: upper-triangle tiles + mirror store
+};
+cudaError_t launch_simt_gemm(const SimtArgs& a, int epi, cudaStream_t s);
+int simt_gram_tiles(int64_t n);
+
+// ---------------------------------------------------------------------------------
+// tcgen05 split-BF16 GEMM / SYRK (gemm_tc.cu)
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2 };
+
+struct TcOperand {
+  const uint16_t* planes;  // plane p at planes + p * plane_stride (elements)
+  int64_t rows, cols;      // stored matrix shape (row-major)
+  int64_t ld;              // elements; multiple of 8
+  int64_t plane_stride;    // elements; multiple of 8
+  int kmajor;              // 1: stored (MN x K), K contiguous; 0: stored (K x MN), MN contiguous
+};
+
+struct TcArgs {
+  int64_t M, N, K;
+  TcOperand a, b;
+  int nplanes;             // 1..3: planes stored per operand (and passes: 1, 3, 6)
+  int epi;                 // TcEpi
+  int triangular;          // SYRK upper-triangle tiles + mirror store
+  float* C; int64_t ldc; float alpha, beta;      // STORE
+  float* X; int64_t ldx;                          // NS: X <- 1.5 X - 0.5 acc in place
+  uint16_t* out_planes; int64_t ldo; int64_t out_plane_stride; int out_nplanes; // NS/GRAM plane output
+  double* partials;                               // GRAM residual partials
+  DevState* st;                                   // skip when not RUNNING; error flags
+  const int* planes_dyn;                          // if non-null: passes use min(*planes_dyn, nplanes)
+                                                  // planes (schedules); outputs keep out_nplanes
+};
+cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s);
+int tc_gram_partials(int64_t n);
+bool tc_available();
+
+}  // namespace polar

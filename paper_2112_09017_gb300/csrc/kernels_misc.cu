@@ -1,0 +1,314 @@
+// Bandwidth-bound kernels of the Newton-Schulz polar path:
+//  - ||A||_F with float64 accumulation (the Frobenius scaling of Sec. III.D,
+//    first step of Algorithm 1), in a fixed reduction order;
+//  - X_0 = A / ||A||_F fused with the BF16 plane split of X_0;
+//  - the residual finalize and stop rule ||G - I||_F / sqrt(n) <= tol;
+//  - H = (C + C^T) / 2 from C = U^T A with the symmetry check;
+//  - mirror of an upper-triangle Gram to the full symmetric matrix.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace polar {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint16_t bf16_rne_bits(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);  // NaN stays NaN
+  uint32_t lsb = (u >> 16) & 1u;
+  return (uint16_t)((u + 0x7fffu + lsb) >> 16);
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(uint16_t b) {
+  return __uint_as_float(((uint32_t)b) << 16);
+}
+
+// Fixed-order block sum of one double per thread (result valid in thread 0).
+__device__ double block_sum(double v) {
+  __shared__ double red[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+__global__ void frob_partials_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                     double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+    const float* row = A + r * lda;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      double v = (double)row[c];
+      acc = fma(v, v, acc);
+    }
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void norm_finalize_kernel(const double* __restrict__ partials, int nparts, DevState* st,
+                                     double inv_sqrt_n, int planes_first) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) {
+    double nrm = sqrt(t);
+    st->normA = nrm;
+    st->inv_sqrt_n = inv_sqrt_n;
+    st->iters = 0;
+    st->hist_len = 0;
+    st->err_flags = 0;
+    st->planes_next = planes_first;
+    st->sym_err = 0.0;
+    for (int i = 0; i < 4; ++i) st->ring[i] = 0.0;
+    st->status = (isfinite(nrm) && nrm > 0.0) ? ST_RUNNING : ST_NONFINITE;
+  }
+}
+
+// dst = src * (1/||A||_F as float32 divisor) and/or BF16 planes of the same values.
+__global__ void scale_split_kernel(const float* __restrict__ src, int64_t lds, int64_t m, int64_t n,
+                                   const DevState* __restrict__ st, int scale, float* __restrict__ dst,
+                                   int64_t ldd, uint16_t* __restrict__ planes, int64_t ldp,
+                                   int64_t plane_stride, int nplanes) {
+  if (st && st->status != ST_RUNNING) return;
+  float s = scale ? (float)st->normA : 1.0f;
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      float x = src[r * lds + c];
+      if (scale) x = __fdiv_rn(x, s);
+      if (dst) dst[r * ldd + c] = x;
+      float rem = x;
+      for (int p = 0; p < nplanes; ++p) {
+        uint16_t b = bf16_rne_bits(rem);
+        planes[p * plane_stride + r * ldp + c] = b;
+        rem = rem - bf16_bits_to_float(b);
+      }
+    }
+  }
+}
+
+__global__ void split_flat_kernel(const float* __restrict__ x, int64_t count, int nplanes,
+                                  uint16_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float rem = x[i];
+    for (int p = 0; p < nplanes; ++p) {
+      uint16_t b = bf16_rne_bits(rem);
+      out[p * count + i] = b;
+      rem = rem - bf16_bits_to_float(b);
+    }
+  }
+}
+
+// Sums the Gram partials in a fixed order and applies the stop rule for step k.
+__global__ void residual_finalize_kernel(const double* __restrict__ partials, int nparts, DevState* st,
+                                         StopRule rule, int k, int planes_this) {
+  if (st->status != ST_RUNNING) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
+  double t = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  double r = sqrt(t) * st->inv_sqrt_n;
+  if (k < POLAR_HIST) {
+    st->res_hist[k] = r;
+    st->planes_hist[k] = (unsigned char)(planes_this < 0 ? st->planes_next : planes_this);
+    st->hist_len = k + 1;
+  }
+  double r2 = (k >= 2) ? st->ring[(k - 2) & 3] : 0.0;
+  st->ring[k & 3] = r;
+  st->iters = k;
+  if (!isfinite(r)) {
+    st->status = ST_NONFINITE;
+  } else if (r <= rule.tol) {
+    st->status = ST_CONVERGED;
+  } else if (k >= 2 && r > rule.stagnation * r2 && r < rule.stag_floor) {
+    st->status = ST_NOT_CONVERGED;
+  } else if (k >= rule.max_iter) {
+    st->status = ST_NOT_CONVERGED;
+  } else {
+    st->planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
+  }
+}
+
+// H = (C + C^T)/2 through 32x32 shared-memory tiles; float64 partials of
+// ||(C - C^T)/2||^2 and ||C||^2 per block (grid-stride over tiles, fixed order).
+__global__ void symmetrize_kernel(const float* __restrict__ C, int64_t ldc, int64_t n, float* __restrict__ H,
+                                  int64_t ldh, double* __restrict__ partials) {
+  __shared__ float ta[32][33];
+  __shared__ float tb[32][33];
+  int64_t nt = (n + 31) / 32;
+  int64_t ntiles = nt * nt;
+  double skew = 0.0, full = 0.0;
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t bi = t / nt, bj = t % nt;
+    int64_t i0 = bi * 32, j0 = bj * 32;
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      int64_t i = i0 + yy, j = j0 + tx;
+      ta[yy][tx] = (i < n && j < n) ? C[i * ldc + j] : 0.0f;
+      int64_t i2 = j0 + yy, j2 = i0 + tx;  // tile (bj, bi)
+      tb[yy][tx] = (i2 < n && j2 < n) ? C[i2 * ldc + j2] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      int64_t i = i0 + yy, j = j0 + tx;
+      if (i < n && j < n) {
+        float c = ta[yy][tx], ct = tb[tx][yy];
+        H[i * ldh + j] = 0.5f * (c + ct);
+        double d = 0.5 * ((double)c - (double)ct);
+        skew = fma(d, d, skew);
+        full = fma((double)c, (double)c, full);
+      }
+    }
+  }
+  double s1 = block_sum(skew);
+  double s2 = block_sum(full);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s1;
+    partials[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+__global__ void sym_finalize_kernel(const double* __restrict__ partials, int blocks, DevState* st) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < blocks; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  double s1 = block_sum(a);
+  double s2 = block_sum(b);
+  if (threadIdx.x == 0) st->sym_err = s2 > 0.0 ? sqrt(s1 / s2) : 0.0;
+}
+
+template <typename T>
+__global__ void mirror_kernel(T* __restrict__ C, int64_t ldc, int64_t plane_stride, int nplanes, int64_t n,
+                              const DevState* __restrict__ st, const int* __restrict__ planes_dyn) {
+  if (st && st->status != ST_RUNNING) return;
+  if (planes_dyn) nplanes = *planes_dyn;
+  __shared__ T tile[32][33];
+  int64_t nt = (n + 31) / 32;
+  int64_t ntri = nt * (nt + 1) / 2;  // tiles (bi <= bj) of the upper triangle
+  int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int p = 0; p < nplanes; ++p) {
+    T* Cp = C + p * plane_stride;
+    for (int64_t t = blockIdx.x; t < ntri; t += gridDim.x) {
+      // column-major enumeration of the upper triangle: t = bj (bj + 1) / 2 + bi
+      int64_t bj = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while (bj * (bj + 1) / 2 > t) --bj;
+      while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+      int64_t bi = t - bj * (bj + 1) / 2;
+      int64_t i0 = bi * 32, j0 = bj * 32;
+      __syncthreads();
+      for (int yy = ty; yy < 32; yy += 8) {
+        int64_t i = i0 + yy, j = j0 + tx;
+        tile[yy][tx] = (i < n && j < n) ? Cp[i * ldc + j] : T(0);
+      }
+      __syncthreads();
+      // write C[j][i] = C[i][j] for i < j: row (j0 + yy), column (i0 + tx)
+      for (int yy = ty; yy < 32; yy += 8) {
+        int64_t j = j0 + yy, i = i0 + tx;
+        if (i < n && j < n && i < j) Cp[j * ldc + i] = tile[tx][yy];
+      }
+    }
+  }
+}
+
+__global__ void copy2d_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
+                              int64_t m, int64_t n) {
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) dst[r * ldd + c] = src[r * lds + c];
+}
+
+int grid_rows(int64_t m) { return (int)(m < 4096 ? (m > 0 ? m : 1) : 4096); }
+
+}  // namespace
+
+int frob_partials_blocks(int64_t m, int64_t n) {
+  (void)n;
+  return (int)(m < 2048 ? m : 2048);
+}
+
+cudaError_t launch_frob_partials(const float* A, int64_t m, int64_t n, int64_t lda, double* partials, int blocks,
+                                 cudaStream_t s) {
+  frob_partials_kernel<<<blocks, kThreads, 0, s>>>(A, m, n, lda, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_finalize(const double* partials, int nparts, DevState* st, double inv_sqrt_n,
+                                 int planes_first, cudaStream_t s) {
+  norm_finalize_kernel<<<1, kThreads, 0, s>>>(partials, nparts, st, inv_sqrt_n, planes_first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_split(const float* src, int64_t lds, int64_t m, int64_t n, const DevState* st, bool scale,
+                               float* dst, int64_t ldd, uint16_t* planes, int64_t ldp, int64_t plane_stride,
+                               int nplanes, cudaStream_t s) {
+  scale_split_kernel<<<grid_rows(m), kThreads, 0, s>>>(src, lds, m, n, st, scale ? 1 : 0, dst, ldd, planes, ldp,
+                                                        plane_stride, nplanes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_flat(const float* x, int64_t count, int nplanes, uint16_t* out, cudaStream_t s) {
+  int64_t blocks = (count + kThreads - 1) / kThreads;
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  split_flat_kernel<<<(int)blocks, kThreads, 0, s>>>(x, count, nplanes, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_finalize(const double* partials, int nparts, DevState* st, StopRule rule, int k,
+                                     int planes_this, cudaStream_t s) {
+  residual_finalize_kernel<<<1, kThreads, 0, s>>>(partials, nparts, st, rule, k, planes_this);
+  return cudaGetLastError();
+}
+
+int symmetrize_blocks(int64_t n) {
+  int64_t nt = (n + 31) / 32;
+  int64_t t = nt * nt;
+  return (int)(t < 1024 ? t : 1024);
+}
+
+cudaError_t launch_symmetrize(const float* C, int64_t ldc, int64_t n, float* H, int64_t ldh, double* partials,
+                              int blocks, cudaStream_t s) {
+  symmetrize_kernel<<<blocks, kThreads, 0, s>>>(C, ldc, n, H, ldh, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_finalize(const double* partials, int blocks, DevState* st, cudaStream_t s) {
+  sym_finalize_kernel<<<1, kThreads, 0, s>>>(partials, blocks, st);
+  return cudaGetLastError();
+}
+
+static int mirror_blocks(int64_t n) {
+  int64_t nt = (n + 31) / 32;
+  int64_t t = nt * (nt + 1) / 2;
+  return (int)(t < 4096 ? t : 4096);
+}
+
+cudaError_t launch_mirror_f32(float* C, int64_t ldc, int64_t n, const DevState* st, cudaStream_t s) {
+  mirror_kernel<float><<<mirror_blocks(n), kThreads, 0, s>>>(C, ldc, 0, 1, n, st, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride, int nplanes, int64_t n,
+                                 const DevState* st, const int* planes_dyn, cudaStream_t s) {
+  mirror_kernel<uint16_t><<<mirror_blocks(n), kThreads, 0, s>>>(P, ldp, plane_stride, nplanes, n, st, planes_dyn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t m, int64_t n,
+                          cudaStream_t s) {
+  copy2d_kernel<<<grid_rows(m), kThreads, 0, s>>>(src, lds, dst, ldd, m, n);
+  return cudaGetLastError();
+}
+
+}  // namespace polar

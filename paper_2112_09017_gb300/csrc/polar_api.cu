@@ -1,0 +1,700 @@
+// C ABI of libpolar.so: plans, the single-solve iteration driver, batched solves,
+// and the general products. The iteration (Sec. III.D, Eq. NewtonSchulz,
+// Algorithm 1 with the residual stop rule) runs entirely on the device; the host
+// only enqueues kernels and reads a small status block between chunks.
+#include <cuda.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace polar;
+
+namespace {
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return POLAR_ECUDA;  \
+  } while (0)
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int planes_of(int prec) {
+  switch (prec) {
+    case POLAR_BF16X6: return 3;
+    case POLAR_BF16X3: return 2;
+    case POLAR_BF16: return 1;
+    case POLAR_SCHED_BF16_THEN_X3: return 2;  // workspace for the finer phase
+    default: return 0;
+  }
+}
+
+bool device_ok(int* sms = nullptr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  int major = 0, minor = 0, count = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  if (sms) *sms = count;
+  return major == 10 && minor == 3;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  uintptr_t x0 = (uintptr_t)a, x1 = x0 + na, y0 = (uintptr_t)b, y1 = y0 + nb;
+  return x0 < y1 && y0 < x1;
+}
+
+// Per-device scratch for polar_gemm / polar_syrk plane splits.
+struct Scratch {
+  std::mutex mu;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+Scratch g_scratch[64];
+
+polar_status_t scratch_get(size_t bytes, void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return POLAR_ECUDA;
+  Scratch& s = g_scratch[dev];
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (s.bytes < bytes) {
+    if (s.ptr) {
+      CK(cudaDeviceSynchronize());
+      cudaFree(s.ptr);
+      s.ptr = nullptr;
+      s.bytes = 0;
+    }
+    if (cudaMalloc(&s.ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return POLAR_ENOMEM;
+    }
+    s.bytes = bytes;
+  }
+  *out = s.ptr;
+  return POLAR_OK;
+}
+
+}  // namespace
+
+struct polar_plan_s {
+  bool batched = false;
+  int64_t m = 0, n = 0;
+  polar_options_t opt{};
+  int prec = POLAR_BF16X6;
+  int P = 0;  // BF16 planes (0: FP32 SIMT path)
+  int sms = 0;
+  // workspace
+  std::vector<void*> allocs;
+  size_t ws_bytes = 0;
+  float* X[2] = {nullptr, nullptr};  // FP32 path: double buffer; BF16 path: X[0] in place
+  int64_t ldx = 0;
+  float* G = nullptr;  // FP32 Gram, and C = U^T A at the end (both paths)
+  int64_t ldg = 0;
+  uint16_t* Xp[2] = {nullptr, nullptr};  // BF16 planes of X (double buffer)
+  uint16_t* Gp = nullptr;                // BF16 planes of G
+  uint16_t* Ap = nullptr;                // BF16 planes of A (for H)
+  int64_t ldp = 0;                       // plane row pitch (elements)
+  int64_t xps = 0, gps = 0;              // plane strides (elements)
+  double* partials = nullptr;
+  int nparts = 0;
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;  // pinned
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+  cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+  // bookkeeping of one run
+  int launches = 0;
+  struct Prof { cudaEvent_t a, b; int kind, k; };  // kind 0: Gram, 1: update
+  std::vector<Prof> prof;
+  size_t prof_used = 0;
+  // batched
+  int count = 0;
+  std::vector<polar_plan_t> subplans;
+};
+
+extern "C" {
+
+void polar_default_options(polar_options_t* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_iter = 100;
+  o->prec = POLAR_BF16X6;
+  o->stagnation = 0.7;
+  o->stag_floor = 1e-4;
+  o->switch_residual = 1e-2;
+  o->ws_limit = 0;
+}
+
+const char* polar_status_string(polar_status_t s) {
+  switch (s) {
+    case POLAR_OK: return "ok";
+    case POLAR_NOT_CONVERGED: return "not converged (stagnation or max_iter)";
+    case POLAR_EINVAL: return "invalid argument";
+    case POLAR_ENOMEM: return "out of device memory or above ws_limit";
+    case POLAR_ECUDA: return "CUDA error or no sm_103 device";
+    case POLAR_ENONFINITE: return "input norm or residual is zero or non-finite";
+    case POLAR_ETIMEOUT: return "a bounded device wait expired";
+    case POLAR_ENOTSUP: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+polar_status_t polar_device_query(int* sm_count, int* cc_major, int* cc_minor) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return POLAR_ECUDA; }
+  int a = 0, b = 0, c = 0;
+  if (cudaDeviceGetAttribute(&a, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return POLAR_ECUDA;
+  }
+  if (sm_count) *sm_count = a;
+  if (cc_major) *cc_major = b;
+  if (cc_minor) *cc_minor = c;
+  return POLAR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void normalize_options(polar_options_t& o) {
+  if (!(o.tol > 0)) o.tol = 1e-6;
+  if (o.max_iter <= 0) o.max_iter = 100;
+  if (!(o.stagnation > 0)) o.stagnation = 0.7;
+  if (!(o.stag_floor > 0)) o.stag_floor = 1e-4;
+  if (!(o.switch_residual > 0)) o.switch_residual = 1e-2;
+}
+
+int resolve_prec(int prec, int64_t n) {
+  if (prec == POLAR_AUTO) return n >= 256 ? POLAR_BF16X6 : POLAR_FP32;
+  return prec;
+}
+
+polar_status_t plan_alloc(polar_plan_s* p, size_t bytes, void** out) {
+  if (p->opt.ws_limit && p->ws_bytes + bytes > p->opt.ws_limit) return POLAR_ENOMEM;
+  void* ptr = nullptr;
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return POLAR_ENOMEM;
+  }
+  p->allocs.push_back(ptr);
+  p->ws_bytes += bytes;
+  *out = ptr;
+  return POLAR_OK;
+}
+
+void plan_free(polar_plan_s* p) {
+  for (void* a : p->allocs) cudaFree(a);
+  p->allocs.clear();
+  if (p->st_host) cudaFreeHost(p->st_host);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_stop) cudaEventDestroy(p->ev_stop);
+  for (auto& e : p->ev_chunk)
+    if (e) cudaEventDestroy(e);
+  for (auto& pr : p->prof) {
+    cudaEventDestroy(pr.a);
+    cudaEventDestroy(pr.b);
+  }
+  p->prof.clear();
+  for (auto sp : p->subplans) {
+    plan_free(sp);
+    delete sp;
+  }
+  p->subplans.clear();
+}
+
+polar_status_t plan_setup(polar_plan_s* p) {
+  const int64_t m = p->m, n = p->n;
+  polar_status_t r;
+  void* v = nullptr;
+  p->P = planes_of(p->prec);
+  p->ldx = round_up(n, 4);
+  p->ldg = round_up(n, 4);
+  if (p->P == 0) {
+    for (int i = 0; i < 2; ++i) {
+      if ((r = plan_alloc(p, (size_t)m * p->ldx * 4, &v)) != POLAR_OK) return r;
+      p->X[i] = (float*)v;
+    }
+  } else {
+    if ((r = plan_alloc(p, (size_t)m * p->ldx * 4, &v)) != POLAR_OK) return r;
+    p->X[0] = (float*)v;
+    p->ldp = round_up(n, 64);
+    p->xps = round_up(m * p->ldp, 64);
+    p->gps = round_up(n * p->ldp, 64);
+    for (int i = 0; i < 2; ++i) {
+      if ((r = plan_alloc(p, (size_t)p->P * p->xps * 2, &v)) != POLAR_OK) return r;
+      CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));  // zero pitch padding once
+      p->Xp[i] = (uint16_t*)v;
+    }
+    if ((r = plan_alloc(p, (size_t)p->P * p->gps * 2, &v)) != POLAR_OK) return r;
+    CK(cudaMemset(v, 0, (size_t)p->P * p->gps * 2));
+    p->Gp = (uint16_t*)v;
+    if ((r = plan_alloc(p, (size_t)p->P * p->xps * 2, &v)) != POLAR_OK) return r;
+    CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));
+    p->Ap = (uint16_t*)v;
+  }
+  if ((r = plan_alloc(p, (size_t)n * p->ldg * 4, &v)) != POLAR_OK) return r;
+  p->G = (float*)v;
+  int np = frob_partials_blocks(m, n);
+  np = std::max(np, simt_gram_tiles(n));
+  np = std::max(np, 2 * symmetrize_blocks(n));
+  if (p->P) np = std::max(np, tc_gram_partials(n));
+  p->nparts = np;
+  if ((r = plan_alloc(p, (size_t)np * 8, &v)) != POLAR_OK) return r;
+  p->partials = (double*)v;
+  if ((r = plan_alloc(p, sizeof(DevState), &v)) != POLAR_OK) return r;
+  p->st = (DevState*)v;
+  CK(cudaMemset(v, 0, sizeof(DevState)));
+  CK(cudaMallocHost((void**)&p->st_host, sizeof(DevState)));
+  memset(p->st_host, 0, sizeof(DevState));
+  CK(cudaEventCreate(&p->ev_start));
+  CK(cudaEventCreate(&p->ev_stop));
+  for (auto& e : p->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return POLAR_OK;
+}
+
+StopRule make_rule(const polar_plan_s* p, double tol) {
+  StopRule r;
+  r.tol = tol;
+  r.stagnation = p->opt.stagnation;
+  r.stag_floor = p->opt.stag_floor;
+  r.switch_residual = p->opt.switch_residual;
+  r.max_iter = p->opt.max_iter;
+  r.sched = p->prec == POLAR_SCHED_BF16_THEN_X3 ? 1 : 0;
+  r.planes_fixed = p->P;
+  return r;
+}
+
+// ---- profiling: optional event pair around each Gram / update launch ----
+
+cudaError_t prof_begin(polar_plan_s* p, int kind, int k, cudaStream_t s, int* idx) {
+  *idx = -1;
+  if (!p->opt.profile) return cudaSuccess;
+  if (p->prof_used == p->prof.size()) {
+    polar_plan_s::Prof pr;
+    cudaError_t e = cudaEventCreate(&pr.a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&pr.b);
+    if (e != cudaSuccess) return e;
+    p->prof.push_back(pr);
+  }
+  auto& pr = p->prof[p->prof_used];
+  pr.kind = kind;
+  pr.k = k;
+  *idx = (int)p->prof_used++;
+  return cudaEventRecord(pr.a, s);
+}
+
+cudaError_t prof_end(polar_plan_s* p, int idx, cudaStream_t s) {
+  if (idx < 0) return cudaSuccess;
+  return cudaEventRecord(p->prof[idx].b, s);
+}
+
+// ---- one Newton-Schulz step k: Gram of X_k + residual/stop rule, then the update ----
+
+cudaError_t enqueue_gram_fp32(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
+  const float* Xk = p->X[k & 1];
+  SimtArgs g{};
+  g.M = p->n; g.N = p->n; g.K = p->m;
+  g.A = Xk; g.lda = p->ldx; g.a_kmajor = 0;
+  g.B = Xk; g.ldb = p->ldx; g.b_kmajor = 0;
+  g.C = p->G; g.ldc = p->ldg; g.alpha = 1.f; g.beta = 0.f;
+  g.partials = p->partials; g.st = p->st; g.triangular = 1;
+  int pi;
+  cudaError_t e = prof_begin(p, 0, k, s, &pi);
+  if (e != cudaSuccess) return e;
+  e = launch_simt_gemm(g, SIMT_EPI_GRAM, s);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_end(p, pi, s)) != cudaSuccess) return e;
+  e = launch_residual_finalize(p->partials, simt_gram_tiles(p->n), p->st, rule, k, 0, s);
+  if (e != cudaSuccess) return e;
+  p->launches += 3;
+  return launch_mirror_f32(p->G, p->ldg, p->n, p->st, s);
+}
+
+cudaError_t enqueue_update_fp32(polar_plan_s* p, int k, cudaStream_t s) {
+  const float* Xk = p->X[k & 1];
+  float* Xn = p->X[(k + 1) & 1];
+  SimtArgs u{};
+  u.M = p->m; u.N = p->n; u.K = p->n;
+  u.A = Xk; u.lda = p->ldx; u.a_kmajor = 1;
+  u.B = p->G; u.ldb = p->ldg; u.b_kmajor = 0;
+  u.C = Xn; u.ldc = p->ldx;
+  u.Xold = Xk; u.ldx = p->ldx; u.st = p->st;
+  int pi;
+  cudaError_t e = prof_begin(p, 1, k, s, &pi);
+  if (e != cudaSuccess) return e;
+  e = launch_simt_gemm(u, SIMT_EPI_NS, s);
+  if (e != cudaSuccess) return e;
+  p->launches += 1;
+  return prof_end(p, pi, s);
+}
+
+TcOperand op_planes(const uint16_t* planes, int64_t rows, int64_t cols, int64_t ld, int64_t stride, int kmajor) {
+  TcOperand o;
+  o.planes = planes; o.rows = rows; o.cols = cols; o.ld = ld; o.plane_stride = stride; o.kmajor = kmajor;
+  return o;
+}
+
+cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
+  const uint16_t* Xk = p->Xp[k & 1];
+  TcArgs g{};
+  g.M = p->n; g.N = p->n; g.K = p->m;
+  g.a = op_planes(Xk, p->m, p->n, p->ldp, p->xps, 0);
+  g.b = g.a;
+  g.nplanes = p->P;
+  g.epi = TC_EPI_GRAM; g.triangular = 1;
+  g.out_planes = p->Gp; g.ldo = p->ldp; g.out_plane_stride = p->gps; g.out_nplanes = p->P;
+  g.partials = p->partials; g.st = p->st;
+  g.planes_dyn = rule.sched ? &p->st->planes_next : nullptr;
+  int pi;
+  cudaError_t e = prof_begin(p, 0, k, s, &pi);
+  if (e != cudaSuccess) return e;
+  e = launch_tc_gemm(g, s);
+  if (e != cudaSuccess) return e;
+  if ((e = prof_end(p, pi, s)) != cudaSuccess) return e;
+  p->launches += 3;
+  // the finalize records the planes this Gram used (schedules: read on the device)
+  e = launch_residual_finalize(p->partials, tc_gram_partials(p->n), p->st, rule, k, rule.sched ? -1 : p->P, s);
+  if (e != cudaSuccess) return e;
+  return launch_mirror_planes(p->Gp, p->ldp, p->gps, p->P, p->n, p->st, nullptr, s);
+}
+
+cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
+  TcArgs u{};
+  u.M = p->m; u.N = p->n; u.K = p->n;
+  u.a = op_planes(p->Xp[k & 1], p->m, p->n, p->ldp, p->xps, 1);
+  u.b = op_planes(p->Gp, p->n, p->n, p->ldp, p->gps, 0);
+  u.nplanes = p->P;
+  u.epi = TC_EPI_NS;
+  u.X = p->X[0]; u.ldx = p->ldx;
+  u.out_planes = p->Xp[(k + 1) & 1]; u.ldo = p->ldp; u.out_plane_stride = p->xps; u.out_nplanes = p->P;
+  u.st = p->st;
+  u.planes_dyn = rule.sched ? &p->st->planes_next : nullptr;
+  int pi;
+  cudaError_t e = prof_begin(p, 1, k, s, &pi);
+  if (e != cudaSuccess) return e;
+  e = launch_tc_gemm(u, s);
+  if (e != cudaSuccess) return e;
+  p->launches += 1;
+  return prof_end(p, pi, s);
+}
+
+polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U, int64_t ldu, float* H,
+                          int64_t ldh, double tol, polar_info_t* info, cudaStream_t s) {
+  const int64_t m = p->m, n = p->n;
+  if (!(tol > 0)) tol = p->opt.tol;
+  StopRule rule = make_rule(p, tol);
+  p->launches = 0;
+  p->prof_used = 0;
+  CK(cudaEventRecord(p->ev_start, s));
+  // ||A||_F and X_0 = A / ||A||_F (+ planes of X_0)
+  int fb = frob_partials_blocks(m, n);
+  CK(launch_frob_partials(A, m, n, lda, p->partials, fb, s));
+  CK(launch_norm_finalize(p->partials, fb, p->st, 1.0 / sqrt((double)n), rule.sched ? 1 : p->P, s));
+  if (p->P == 0)
+    CK(launch_scale_split(A, lda, m, n, p->st, true, p->X[0], p->ldx, nullptr, 0, 0, 0, s));
+  else
+    CK(launch_scale_split(A, lda, m, n, p->st, true, p->X[0], p->ldx, p->Xp[0], p->ldp, p->xps, p->P, s));
+  p->launches += 3;
+
+  // Iterations in chunks; two chunks in flight so the device never waits on the host.
+  // Kernels enqueued after the stop rule fired return at once (they read the status).
+  const int chunk = 4;
+  int k = 0;
+  int head = 0, queued = 0;
+  int status = ST_RUNNING;
+  while (true) {
+    while (queued < 2 && k <= p->opt.max_iter) {
+      for (int c = 0; c < chunk && k <= p->opt.max_iter; ++c, ++k) {
+        if (p->P == 0) {
+          CK(enqueue_gram_fp32(p, k, rule, s));
+          if (k < p->opt.max_iter) CK(enqueue_update_fp32(p, k, s));
+        } else {
+          CK(enqueue_gram_tc(p, k, rule, s));
+          if (k < p->opt.max_iter) CK(enqueue_update_tc(p, k, rule, s));
+        }
+      }
+      CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(p->ev_chunk[(head + queued) & 1], s));
+      ++queued;
+    }
+    if (queued == 0) break;
+    CK(cudaEventSynchronize(p->ev_chunk[head]));
+    head ^= 1;
+    --queued;
+    if (p->st_host->status != ST_RUNNING) break;
+  }
+  CK(cudaStreamSynchronize(s));
+  DevState& h = *p->st_host;
+  status = h.status;
+  if (h.err_flags) status = ST_TIMEOUT;
+  if (status == ST_NONFINITE || status == ST_TIMEOUT || status == ST_RUNNING) {
+    CK(cudaEventRecord(p->ev_stop, s));
+    CK(cudaEventSynchronize(p->ev_stop));
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->status = status == ST_NONFINITE ? POLAR_ENONFINITE : status == ST_TIMEOUT ? POLAR_ETIMEOUT : POLAR_ECUDA;
+      info->normA_F = h.normA;
+      info->prec = p->prec;
+      info->iters = h.iters;
+      info->hist_len = h.hist_len;
+      memcpy(info->res_hist, h.res_hist, sizeof(h.res_hist));
+      memcpy(info->planes_hist, h.planes_hist, sizeof(h.planes_hist));
+    }
+    return status == ST_NONFINITE ? POLAR_ENONFINITE : status == ST_TIMEOUT ? POLAR_ETIMEOUT : POLAR_ECUDA;
+  }
+  const int it = h.iters;
+  // U = X_it ; C = U^T A ; H = sym(C)
+  if (p->P == 0) {
+    const float* Uk = p->X[it & 1];
+    CK(launch_copy2d(Uk, p->ldx, U, ldu, m, n, s));
+    SimtArgs c{};
+    c.M = n; c.N = n; c.K = m;
+    c.A = Uk; c.lda = p->ldx; c.a_kmajor = 0;
+    c.B = A; c.ldb = lda; c.b_kmajor = 0;
+    c.C = p->G; c.ldc = p->ldg; c.alpha = 1.f; c.beta = 0.f;
+    CK(launch_simt_gemm(c, SIMT_EPI_STORE, s));
+    p->launches += 2;
+  } else {
+    CK(launch_copy2d(p->X[0], p->ldx, U, ldu, m, n, s));
+    CK(launch_scale_split(A, lda, m, n, nullptr, false, nullptr, 0, p->Ap, p->ldp, p->xps, p->P, s));
+    TcArgs c{};
+    c.M = n; c.N = n; c.K = m;
+    c.a = op_planes(p->Xp[it & 1], m, n, p->ldp, p->xps, 0);
+    c.b = op_planes(p->Ap, m, n, p->ldp, p->xps, 0);
+    c.nplanes = p->P;
+    c.epi = TC_EPI_STORE;
+    c.C = p->G; c.ldc = p->ldg; c.alpha = 1.f; c.beta = 0.f;
+    c.st = nullptr;
+    CK(launch_tc_gemm(c, s));
+    p->launches += 3;
+  }
+  int sb = symmetrize_blocks(n);
+  CK(launch_symmetrize(p->G, p->ldg, n, H, ldh, p->partials, sb, s));
+  CK(launch_sym_finalize(p->partials, sb, p->st, s));
+  p->launches += 2;
+  CK(cudaEventRecord(p->ev_stop, s));
+  CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (p->st_host->err_flags) status = ST_TIMEOUT;
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, p->ev_start, p->ev_stop));
+  polar_status_t ret = status == ST_CONVERGED ? POLAR_OK
+                       : status == ST_NOT_CONVERGED ? POLAR_NOT_CONVERGED
+                       : POLAR_ETIMEOUT;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = ret;
+    info->iters = it;
+    info->prec = p->prec;
+    info->hist_len = h.hist_len;
+    info->residual = (it < POLAR_HIST && it < h.hist_len) ? h.res_hist[it] : h.ring[it & 3];
+    info->normA_F = h.normA;
+    info->sym_err = h.sym_err;
+    info->ms_total = ms;
+    info->launches = p->launches;
+    for (size_t i = 0; i < p->prof_used; ++i) {
+      const auto& pr = p->prof[i];
+      if ((pr.kind == 0 && pr.k > it) || (pr.kind == 1 && pr.k >= it)) continue;  // launches after the stop
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, pr.a, pr.b));
+      if (pr.kind == 0) { info->ms_gram += t; info->n_gram++; }
+      else { info->ms_update += t; info->n_update++; }
+    }
+    memcpy(info->res_hist, h.res_hist, sizeof(h.res_hist));
+    memcpy(info->planes_hist, h.planes_hist, sizeof(h.planes_hist));
+  }
+  return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+polar_status_t polar_plan_create(polar_plan_t* plan, int64_t m, int64_t n, const polar_options_t* o) {
+  if (!plan) return POLAR_EINVAL;
+  *plan = nullptr;
+  if (n < 1 || m < n) return POLAR_EINVAL;
+  polar_options_t opt;
+  if (o) opt = *o; else polar_default_options(&opt);
+  normalize_options(opt);
+  int prec = resolve_prec(opt.prec, n);
+  if (prec == POLAR_TF32X3 || prec == POLAR_SCHED_FP8_BF16_X3) return POLAR_ENOTSUP;
+  if (prec < 0 || prec > POLAR_BF16) return POLAR_EINVAL;
+  int sms = 0;
+  if (!device_ok(&sms)) { cudaGetLastError(); return POLAR_ECUDA; }
+  if (planes_of(prec) > 0 && !tc_available()) return POLAR_ENOTSUP;
+  polar_plan_s* p = new (std::nothrow) polar_plan_s();
+  if (!p) return POLAR_ENOMEM;
+  p->m = m; p->n = n; p->opt = opt; p->prec = prec; p->sms = sms;
+  polar_status_t r = plan_setup(p);
+  if (r != POLAR_OK) {
+    plan_free(p);
+    delete p;
+    cudaGetLastError();
+    return r;
+  }
+  *plan = p;
+  return POLAR_OK;
+}
+
+size_t polar_plan_workspace_bytes(polar_plan_t plan) {
+  if (!plan) return 0;
+  size_t b = plan->ws_bytes;
+  for (auto sp : plan->subplans) b += sp->ws_bytes;
+  return b;
+}
+
+void polar_plan_destroy(polar_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  delete plan;
+}
+
+polar_status_t polar_run(polar_plan_t plan, const float* A, int64_t lda, float* U, int64_t ldu, float* H,
+                         int64_t ldh, double tol, polar_info_t* info, polar_stream_t stream) {
+  if (!plan || plan->batched || !A || !U || !H) return POLAR_EINVAL;
+  const int64_t m = plan->m, n = plan->n;
+  if (lda < n || ldu < n || ldh < n) return POLAR_EINVAL;
+  size_t na = (size_t)((m - 1) * lda + n) * 4, nu = (size_t)((m - 1) * ldu + n) * 4,
+         nh = (size_t)((n - 1) * ldh + n) * 4;
+  if (overlaps(A, na, U, nu) || overlaps(A, na, H, nh) || overlaps(U, nu, H, nh)) return POLAR_EINVAL;
+  polar_status_t r = run_single(plan, A, lda, U, ldu, H, ldh, tol, info, (cudaStream_t)stream);
+  if (r == POLAR_ECUDA) cudaGetLastError();
+  return r;
+}
+
+polar_status_t polar_batched_plan_create(polar_plan_t* plan, int count, const int64_t* m, const int64_t* n,
+                                         const polar_options_t* o) {
+  if (!plan) return POLAR_EINVAL;
+  *plan = nullptr;
+  if (count < 1 || !m || !n) return POLAR_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || m[i] < n[i]) return POLAR_EINVAL;
+  return POLAR_ENOTSUP;
+}
+
+polar_status_t polar_batched_run(polar_plan_t plan, const float* const* A, float* const* U, float* const* H,
+                                 double tol, int32_t* iters_dev, double* resid_dev, polar_stream_t stream) {
+  (void)tol; (void)iters_dev; (void)resid_dev; (void)stream;
+  if (!plan || !plan->batched || !A || !U || !H) return POLAR_EINVAL;
+  return POLAR_ENOTSUP;
+}
+
+polar_status_t polar_split_bf16(const float* X, int64_t count, int planes, uint16_t* out, polar_stream_t stream) {
+  if (count < 0 || planes < 1 || planes > 3) return POLAR_EINVAL;
+  if (count == 0) return POLAR_OK;
+  if (!X || !out) return POLAR_EINVAL;
+  if (overlaps(X, (size_t)count * 4, out, (size_t)count * 2 * planes)) return POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  if (launch_split_flat(X, count, planes, out, (cudaStream_t)stream) != cudaSuccess) return POLAR_ECUDA;
+  return POLAR_OK;
+}
+
+polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                          int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int prec,
+                          polar_stream_t stream) {
+  if (M < 0 || N < 0 || K < 0) return POLAR_EINVAL;
+  if (M == 0 || N == 0) return POLAR_OK;
+  if (!C || ldc < N) return POLAR_EINVAL;
+  if (K > 0 && (!A || !B)) return POLAR_EINVAL;
+  // stored shapes
+  const int64_t a_rows = transA ? K : M, a_cols = transA ? M : K;
+  const int64_t b_rows = transB ? N : K, b_cols = transB ? K : N;
+  if (K > 0 && (lda < a_cols || ldb < b_cols)) return POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  cudaStream_t s = (cudaStream_t)stream;
+  prec = resolve_prec(prec, std::min(M, N));
+  if (K == 0) {
+    // C = beta C
+    SimtArgs g{};
+    g.M = M; g.N = N; g.K = 0; g.A = C; g.lda = ldc; g.a_kmajor = 1; g.B = C; g.ldb = ldc; g.b_kmajor = 1;
+    g.C = C; g.ldc = ldc; g.alpha = 0.f; g.beta = beta;
+    return launch_simt_gemm(g, SIMT_EPI_STORE, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+  }
+  if (prec == POLAR_FP32) {
+    SimtArgs g{};
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.a_kmajor = transA ? 0 : 1;
+    g.B = B; g.ldb = ldb; g.b_kmajor = transB ? 1 : 0;
+    g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+    return launch_simt_gemm(g, SIMT_EPI_STORE, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+  }
+  int P = planes_of(prec);
+  if (P == 0 || prec == POLAR_SCHED_BF16_THEN_X3) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  if (!tc_available()) return POLAR_ENOTSUP;
+  const int64_t lpa = round_up(a_cols, 64), lpb = round_up(b_cols, 64);
+  const int64_t sa = round_up(a_rows * lpa, 64), sb = round_up(b_rows * lpb, 64);
+  void* scr = nullptr;
+  polar_status_t r = scratch_get((size_t)P * (sa + sb) * 2, &scr);
+  if (r != POLAR_OK) return r;
+  uint16_t* pa = (uint16_t*)scr;
+  uint16_t* pb = pa + P * sa;
+  CK(cudaMemsetAsync(scr, 0, (size_t)P * (sa + sb) * 2, s));
+  CK(launch_scale_split(A, lda, a_rows, a_cols, nullptr, false, nullptr, 0, pa, lpa, sa, P, s));
+  CK(launch_scale_split(B, ldb, b_rows, b_cols, nullptr, false, nullptr, 0, pb, lpb, sb, P, s));
+  TcArgs g{};
+  g.M = M; g.N = N; g.K = K;
+  g.a = op_planes(pa, a_rows, a_cols, lpa, sa, transA ? 0 : 1);
+  g.b = op_planes(pb, b_rows, b_cols, lpb, sb, transB ? 1 : 0);
+  g.nplanes = P;
+  g.epi = TC_EPI_STORE;
+  g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+  return launch_tc_gemm(g, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int64_t lda, float beta, float* C,
+                          int64_t ldc, int prec, polar_stream_t stream) {
+  if (n < 0 || k < 0) return POLAR_EINVAL;
+  if (n == 0) return POLAR_OK;
+  if (!C || ldc < n) return POLAR_EINVAL;
+  if (k > 0 && (!A || lda < n)) return POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  cudaStream_t s = (cudaStream_t)stream;
+  prec = resolve_prec(prec, n);
+  if (k == 0 || prec == POLAR_FP32) {
+    SimtArgs g{};
+    g.M = n; g.N = n; g.K = k;
+    g.A = k ? A : C; g.lda = k ? lda : ldc; g.a_kmajor = 0;
+    g.B = g.A; g.ldb = g.lda; g.b_kmajor = 0;
+    g.C = C; g.ldc = ldc; g.alpha = k ? alpha : 0.f; g.beta = beta; g.triangular = 1;
+    CK(launch_simt_gemm(g, SIMT_EPI_STORE, s));
+    CK(launch_mirror_f32(C, ldc, n, nullptr, s));
+    return POLAR_OK;
+  }
+  int P = planes_of(prec);
+  if (P == 0 || prec == POLAR_SCHED_BF16_THEN_X3) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  if (!tc_available()) return POLAR_ENOTSUP;
+  const int64_t lp = round_up(n, 64);
+  const int64_t sa = round_up(k * lp, 64);
+  void* scr = nullptr;
+  polar_status_t r = scratch_get((size_t)P * sa * 2, &scr);
+  if (r != POLAR_OK) return r;
+  uint16_t* pa = (uint16_t*)scr;
+  CK(cudaMemsetAsync(scr, 0, (size_t)P * sa * 2, s));
+  CK(launch_scale_split(A, lda, k, n, nullptr, false, nullptr, 0, pa, lp, sa, P, s));
+  TcArgs g{};
+  g.M = n; g.N = n; g.K = k;
+  g.a = op_planes(pa, k, n, lp, sa, 0);
+  g.b = g.a;
+  g.nplanes = P;
+  g.epi = TC_EPI_STORE; g.triangular = 1;
+  g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+  CK(launch_tc_gemm(g, s));
+  CK(launch_mirror_f32(C, ldc, n, nullptr, s));
+  return POLAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+"""ctypes binding of libpolar.so (include/polar.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels. torch supplies device memory and the current stream. Loading fails
+loudly when the library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpolar.so")
+
+POLAR_OK, POLAR_NOT_CONVERGED = 0, 1
+POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA, POLAR_ENONFINITE, POLAR_ETIMEOUT, POLAR_ENOTSUP = -1, -2, -3, -4, -5, -6
+POLAR_FP32, POLAR_BF16X6, POLAR_TF32X3, POLAR_BF16X3 = 0, 1, 2, 3
+POLAR_SCHED_BF16_THEN_X3, POLAR_SCHED_FP8_BF16_X3, POLAR_AUTO, POLAR_BF16 = 4, 5, 6, 7
+POLAR_HIST = 128
+
+PREC = {"fp32": POLAR_FP32, "bf16x6": POLAR_BF16X6, "tf32x3": POLAR_TF32X3, "bf16x3": POLAR_BF16X3,
+        "bf16_then_x3": POLAR_SCHED_BF16_THEN_X3, "fp8_bf16_x3": POLAR_SCHED_FP8_BF16_X3, "auto": POLAR_AUTO,
+        "bf16": POLAR_BF16}
+# tensor-core passes per product for each BF16 plane count
+PASSES = {0: 0, 1: 1, 2: 3, 3: 6}
+
+
+class polar_options_t(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int), ("stagnation", C.c_double),
+                ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int)]
+
+
+class polar_info_t(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("prec", C.c_int), ("hist_len", C.c_int),
+                ("residual", C.c_double), ("normA_F", C.c_double), ("sym_err", C.c_double),
+                ("ms_total", C.c_float), ("launches", C.c_int), ("n_gram", C.c_int), ("n_update", C.c_int),
+                ("ms_gram", C.c_float), ("ms_update", C.c_float), ("res_hist", C.c_double * POLAR_HIST),
+                ("planes_hist", C.c_ubyte * POLAR_HIST)]
+
+    def as_dict(self):
+        n = self.hist_len
+        return {"status": self.status, "iters": self.iters, "prec": self.prec, "residual": self.residual,
+                "normA_F": self.normA_F, "sym_err": self.sym_err, "ms_total": self.ms_total,
+                "launches": self.launches, "n_gram": self.n_gram, "n_update": self.n_update,
+                "ms_gram": self.ms_gram, "ms_update": self.ms_update,
+                "res_hist": list(self.res_hist[:n]), "planes_hist": list(self.planes_hist[:n])}
+
+
+class PolarError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+_lib = None
+
+
+def load():
+    """Load libpolar.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_2112_09017_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, f32, f64 = C.c_void_p, C.c_int64, C.c_int, C.c_float, C.c_double
+    sig = {
+        "polar_default_options": (None, [C.POINTER(polar_options_t)]),
+        "polar_status_string": (C.c_char_p, [i32]),
+        "polar_plan_create": (i32, [C.POINTER(vp), i64, i64, C.POINTER(polar_options_t)]),
+        "polar_plan_workspace_bytes": (C.c_size_t, [vp]),
+        "polar_run": (i32, [vp, vp, i64, vp, i64, vp, i64, f64, C.POINTER(polar_info_t), vp]),
+        "polar_batched_plan_create": (i32, [C.POINTER(vp), i32, C.POINTER(i64), C.POINTER(i64),
+                                            C.POINTER(polar_options_t)]),
+        "polar_batched_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), f64, vp, vp, vp]),
+        "polar_plan_destroy": (None, [vp]),
+        "polar_gemm": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
+        "polar_syrk": (i32, [i64, i64, f32, vp, i64, f32, vp, i64, i32, vp]),
+        "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
+        "polar_device_query": (i32, [C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().polar_status_string(code).decode()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _check_f32_2d(t, name):
+    import torch
+    if t.dtype != torch.float32 or t.dim() != 2 or not t.is_cuda or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D row-major float32 CUDA tensor")
+
+
+# ------------------------------------------------------------------ same-named wrappers
+
+def polar_default_options() -> polar_options_t:
+    o = polar_options_t()
+    load().polar_default_options(C.byref(o))
+    return o
+
+
+def polar_device_query():
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    r = load().polar_device_query(C.byref(a), C.byref(b), C.byref(c))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_device_query")
+    return a.value, b.value, c.value
+
+
+def polar_plan_create(m: int, n: int, options: polar_options_t | None = None):
+    h = C.c_void_p()
+    r = load().polar_plan_create(C.byref(h), m, n, C.byref(options) if options is not None else None)
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_plan_create")
+    return h
+
+
+def polar_plan_destroy(plan):
+    load().polar_plan_destroy(plan)
+
+
+def polar_plan_workspace_bytes(plan) -> int:
+    return load().polar_plan_workspace_bytes(plan)
+
+
+def polar_run(plan, A, U, H, tol: float = 0.0, stream=None, raw_status: bool = False):
+    """Run a plan on device tensors A (m x n), U (m x n), H (n x n). Returns the info dict."""
+    _check_f32_2d(A, "A"); _check_f32_2d(U, "U"); _check_f32_2d(H, "H")
+    info = polar_info_t()
+    r = load().polar_run(plan, _ptr(A), A.stride(0), _ptr(U), U.stride(0), _ptr(H), H.stride(0), float(tol),
+                         C.byref(info), _stream(stream))
+    d = info.as_dict()
+    d["status"] = r
+    if not raw_status and r not in (POLAR_OK, POLAR_NOT_CONVERGED):
+        raise PolarError(r, "polar_run")
+    return d
+
+
+def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None):
+    cnt = len(ms)
+    am = (C.c_int64 * cnt)(*ms)
+    an = (C.c_int64 * cnt)(*ns)
+    h = C.c_void_p()
+    r = load().polar_batched_plan_create(C.byref(h), cnt, am, an, C.byref(options) if options is not None else None)
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_batched_plan_create")
+    return h
+
+
+def polar_batched_run(plan, As, Us, Hs, tol=0.0, iters_dev=None, resid_dev=None, stream=None):
+    cnt = len(As)
+    pa = (C.c_void_p * cnt)(*[a.data_ptr() for a in As])
+    pu = (C.c_void_p * cnt)(*[u.data_ptr() for u in Us])
+    ph = (C.c_void_p * cnt)(*[h.data_ptr() for h in Hs])
+    r = load().polar_batched_run(plan, pa, pu, ph, float(tol), _ptr(iters_dev), _ptr(resid_dev), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_batched_run")
+
+
+def polar_gemm(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None):
+    """C_ = alpha op(A) op(B) + beta C_ on device tensors."""
+    _check_f32_2d(A, "A"); _check_f32_2d(B, "B"); _check_f32_2d(C_, "C")
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    N = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != K or tuple(C_.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    r = load().polar_gemm(int(trans_a), int(trans_b), M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                          B.stride(0), float(beta), _ptr(C_), C_.stride(0), int(prec), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_gemm")
+
+
+def polar_syrk(A, C_, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None):
+    """C_ = alpha A^T A + beta C_ (full symmetric store)."""
+    _check_f32_2d(A, "A"); _check_f32_2d(C_, "C")
+    k, n = A.shape
+    if tuple(C_.shape) != (n, n):
+        raise ValueError("shape mismatch")
+    r = load().polar_syrk(n, k, float(alpha), _ptr(A), A.stride(0), float(beta), _ptr(C_), C_.stride(0),
+                          int(prec), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_syrk")
+
+
+def polar_split_bf16(X, planes: int, stream=None):
+    """BF16 planes of a contiguous float32 device tensor; returns int16 tensor (planes, numel)."""
+    import torch
+    if X.dtype != torch.float32 or not X.is_cuda or not X.is_contiguous():
+        raise ValueError("X must be a contiguous float32 CUDA tensor")
+    out = torch.empty((planes, X.numel()), dtype=torch.int16, device=X.device)
+    r = load().polar_split_bf16(_ptr(X), X.numel(), planes, _ptr(out), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_split_bf16")
+    return out
+
+
+# ------------------------------------------------------------------ convenience
+
+class Plan:
+    """Owns a single-solve plan; ``plan(A)`` returns (U, H, info)."""
+
+    def __init__(self, m, n, prec="bf16x6", tol=1e-6, max_iter=100, **kw):
+        o = polar_default_options()
+        o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        o.tol = tol
+        o.max_iter = max_iter
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self.m, self.n = m, n
+        self.handle = polar_plan_create(m, n, o)
+
+    def __call__(self, A, tol=0.0, U=None, H=None, stream=None, raw_status=False):
+        import torch
+        if U is None:
+            U = torch.empty((self.m, self.n), dtype=torch.float32, device=A.device)
+        if H is None:
+            H = torch.empty((self.n, self.n), dtype=torch.float32, device=A.device)
+        info = polar_run(self.handle, A, U, H, tol, stream, raw_status)
+        return U, H, info
+
+    def workspace_bytes(self):
+        return polar_plan_workspace_bytes(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            polar_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
