@@ -1,11 +1,648 @@
-// tcgen05 split-BF16 GEMM / SYRK: placeholder until the tensor-core kernel lands.
+// Split-BF16 GEMM / SYRK on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The products of the Newton-Schulz step (Eq. NewtonSchulz: G = X^T X and
+// X' = 1.5 X - 0.5 X G) and U^T A for H, with FP32 operands given as P BF16
+// planes (x = x_0 + x_1 + x_2). Each k-slice of every plane of both operands is
+// staged once in shared memory and all plane-pair passes are issued on it
+// (P = 3: hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid), accumulating into one
+// FP32 TMEM accumulator, so the split costs tensor-pipe time but not extra
+// global or L2 traffic per pass.
+//
+// The tensor cores add into their FP32 accumulator with round-toward-zero
+// (inside one MMA and across MMAs), so a long accumulation drifts toward zero
+// by about half an ulp per step. The kernel therefore accumulates each 32-wide
+// k-slice into a fresh TMEM buffer, issuing the small plane pairs first and
+// hi*hi last (the truncations of the small passes happen at 2^-8 of the
+// result's scale), and the epilogue warps add every slice into FP32 registers
+// with round-to-nearest ("promotion").
+//
+// Structure (one CTA per SM, persistent over output tiles of 128 x 256):
+//   warp 0      TMA producer: cp.async.bulk.tensor 3-D loads (columns, rows,
+//               planes) into a ring of shared-memory stages, mbarrier tx count
+//   warp 1      TMEM allocator and MMA issuer: tcgen05.mma kind::f16 M128 N256
+//               K16 into two alternating 256-column slice buffers; commits free
+//               the stage and publish the slice
+//   warps 2..9  epilogue: two warps per TMEM lane quarter, 128 columns each;
+//               tcgen05.ld of every slice, running sums in registers, then the
+//               fused output step of the tile:
+//                 STORE  C = alpha acc + beta C   (optionally upper triangle)
+//                 NS     X <- 1.5 X - 0.5 acc in place, plus its BF16 planes
+//                 GRAM   BF16 planes of G (upper triangle) and float64
+//                        partials of ||G - I||_F^2 per tile and warp
+// Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-slices)
+// or MN-major (stored K x MN, 128-byte swizzle, 64-element MN chunks).
+// Every mbarrier wait is bounded (about one second); on expiry the kernel
+// records an error flag, lets its copies and MMAs drain, frees TMEM and returns.
+#include <cuda.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "device_util.cuh"
 #include "internal.cuh"
 
 namespace polar {
-bool tc_available() { return false; }
-int tc_gram_partials(int64_t n) { (void)n; return 1; }
-cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s) {
-  (void)a; (void)s;
-  return cudaErrorNotSupported;
+
+__device__ unsigned int g_tc_error;  // timeouts of launches without a plan state
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr uint32_t A_PLANE = BM * BK * 2;  // 8 KiB per plane per stage
+constexpr uint32_t B_PLANE = BN * BK * 2;  // 16 KiB
+constexpr uint32_t TMEM_COLS = 512;        // two 128 x 256 FP32 slice accumulators
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+
+template <int P>
+struct Cfg {
+  static constexpr int STAGES = P == 3 ? 3 : (P == 2 ? 4 : 8);
+  static constexpr uint32_t A_BYTES = P * A_PLANE;
+  static constexpr uint32_t B_BYTES = P * B_PLANE;
+  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t NBARS = 2 * STAGES + 5;
+  static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 + 8 * NBARS + 16;
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity. Returns false when the
+// limit expires (and raises the CTA's abort flag) or another role aborted.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 63u) == 0) {
+      if (abort_flag && *abort_flag) return false;
+      if (gtime() - t0 > WAIT_LIMIT_NS) {
+        if (abort_flag) *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Wait used on the way out after an abort: bounded, ignores the abort flag.
+__device__ __noinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = gtime();
+  while (!mbar_try(bar, parity))
+    if (gtime() - t0 > WAIT_LIMIT_NS / 4) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor for tcgen05.mma (version 1; no base offset).
+// swz: 2 = 128-byte swizzle, 4 = 64-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)swz << 61;
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = BF16, M = 128, N = 256, majors as given.
+__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// Plane pairs of the split product in issue order for `np` planes: the smallest
+// terms first, hi*hi last (6 passes: (1,1) (0,2) (2,0) (0,1) (1,0) (0,0)).
+__device__ __forceinline__ void pass_planes(int np, int i, int& pa, int& pb) {
+  const int first = np == 1 ? 5 : (np == 2 ? 3 : 0);
+  const int j = first + i;
+  pa = (j == 0) ? 1 : (j == 1) ? 0 : (j == 2) ? 2 : (j == 3) ? 0 : (j == 4) ? 1 : 0;
+  pb = (j == 0) ? 1 : (j == 1) ? 2 : (j == 2) ? 0 : (j == 3) ? 1 : (j == 4) ? 0 : 0;
+}
+
+__host__ __device__ __forceinline__ int passes_for(int planes) { return planes == 1 ? 1 : (planes == 2 ? 3 : 6); }
+
+// ---------------------------------------------------------------- tile schedule
+
+__host__ __device__ __forceinline__ int64_t tri_tiles(int64_t tm, int64_t tn) {
+  // column bj of 256 holds row-tiles bi <= 2 bj + 1 (rows of 128), clipped to tm
+  return (tn - 1) * tn + ((2 * tn) < tm ? 2 * tn : tm);
+}
+
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t tm, int64_t tn, bool tri, int64_t& bi, int64_t& bj) {
+  if (tri) {
+    int64_t j = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (j > 0 && j * (j + 1) > t) --j;
+    while ((j + 1) * (j + 2) <= t) ++j;
+    bj = j;
+    bi = t - j * (j + 1);
+  } else {
+    const int64_t G = 16;
+    int64_t group = t / (G * tn);
+    int64_t first = group * G;
+    int64_t rows = (tm - first) < G ? (tm - first) : G;
+    int64_t in = t % (G * tn);
+    bi = first + in % rows;
+    bj = in / rows;
+  }
+}
+
+// ---------------------------------------------------------------- epilogue pieces
+
+__device__ __forceinline__ void store_planes32(uint16_t* base, int64_t pstride, int np, const float* x) {
+  // x: 32 consecutive values; writes np planes, 64 bytes each, 16-byte aligned
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    uint32_t w[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint16_t a[3], b[3];
+      split_planes_dev<3>(x[8 * v + 2 * i], a);
+      split_planes_dev<3>(x[8 * v + 2 * i + 1], b);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) w[q][i] = (uint32_t)a[q] | ((uint32_t)b[q] << 16);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (q < np) reinterpret_cast<uint4*>(base + q * pstride)[v] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+}
+
+__device__ __forceinline__ void store_planes1(uint16_t* base, int64_t pstride, int np, float x) {
+  uint16_t a[3];
+  split_planes_dev<3>(x, a);
+  for (int q = 0; q < np; ++q) base[q * pstride] = a[q];
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <int P, bool A_MN, bool B_MN, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p,
+                   int64_t tm, int64_t tn, int64_t ntiles) {
+  using C = Cfg<P>;
+  constexpr int S = C::STAGES;
+  if (p.st && p.st->status != ST_RUNNING) return;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t smem_base = smem_u32(smem);
+  auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty_bar = [&](int s) { return smem_u32(&bars[S + s]); };
+  auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * S + a]); };
+  auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * S + 2 + a]); };
+  const uint32_t drain_bar = smem_u32(&bars[2 * S + 4]);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), EPI_WARPS);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const bool tri = p.triangular != 0;
+  const int64_t nk = (p.K + BK - 1) / BK;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) armed[s] = -1;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int64_t bi, bj;
+        tile_coords(t, tm, tn, tri, bi, bj);
+        const int m0 = (int)(bi * BM), n0 = (int)(bj * BN);
+        for (int64_t kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
+          const uint32_t fb = full_bar(stage);
+          mbar_expect_tx(fb, C::STAGE_BYTES);
+          armed[stage] = (int)phase;
+          const uint32_t a_dst = smem_base + stage * C::STAGE_BYTES;
+          const uint32_t b_dst = a_dst + C::A_BYTES;
+          const int k0 = (int)(kb * BK);
+          if (A_MN) {
+#pragma unroll
+            for (int c = 0; c < BM / 64; ++c) tma_load_3d(a_dst + c * P * 4096, &tmA, fb, m0 + 64 * c, k0, 0);
+          } else {
+            tma_load_3d(a_dst, &tmA, fb, k0, m0, 0);
+          }
+          if (B_MN) {
+#pragma unroll
+            for (int c = 0; c < BN / 64; ++c) tma_load_3d(b_dst + c * P * 4096, &tmB, fb, n0 + 64 * c, k0, 0);
+          } else {
+            tma_load_3d(b_dst, &tmB, fb, k0, n0, 0);
+          }
+          if (++stage == S) { stage = 0; phase ^= 1u; }
+        }
+      }
+      // let every copy this thread started land before the CTA can exit
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (armed[s] >= 0) mbar_drain(full_bar(s), (uint32_t)armed[s]);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const int pu = p.planes_dyn ? min(max(*p.planes_dyn, 1), P) : P;
+      const int npass = passes_for(pu);
+      constexpr uint32_t idesc = make_idesc(A_MN, B_MN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t buf_phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int64_t kb = 0; kb < nk; ++kb) {
+          // one k-slice into a fresh slice buffer, published to the epilogue
+          if (!mbar_wait(tempty_bar(buf), buf_phase ^ 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(full_bar(stage), phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+          const uint32_t a_st = smem_base + stage * C::STAGE_BYTES;
+          const uint32_t b_st = a_st + C::A_BYTES;
+          for (int ps = 0; ps < npass; ++ps) {
+            int pa, pb;
+            pass_planes(pu, ps, pa, pb);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              uint64_t ad, bd;
+              if (A_MN) ad = smem_desc(a_st + pa * 4096 + kk * 2048, P * 4096, 1024, 2);
+              else      ad = smem_desc(a_st + pa * A_PLANE + kk * 32, 16, 512, 4);
+              if (B_MN) bd = smem_desc(b_st + pb * 4096 + kk * 2048, P * 4096, 1024, 2);
+              else      bd = smem_desc(b_st + pb * B_PLANE + kk * 32, 16, 512, 4);
+              tc_mma(d_tmem, ad, bd, idesc, (ps > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc_commit(empty_bar(stage));
+          tc_commit(tfull_bar(buf));
+          if (++stage == S) { stage = 0; phase ^= 1u; }
+          if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+        }
+      }
+      // every MMA issued so far completes before TMEM is released
+      tc_commit(drain_bar);
+      mbar_drain(drain_bar, 0);
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..9)
+    const int q = warp & 3;                  // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;        // which 128 of the tile's 256 columns
+    const int row_in_tile = q * 32 + lane;
+    const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
+    int buf = 0;
+    uint32_t buf_phase = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int64_t bi, bj;
+      tile_coords(t, tm, tn, tri, bi, bj);
+      float acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+      for (int64_t kb = 0; kb < nk; ++kb) {
+        if (!mbar_wait(tfull_bar(buf), buf_phase, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float v[16];
+          tmem_ld16(t_lane + (uint32_t)(buf * BN + c * 16), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[c * 16 + j] += v[j];   // round-to-nearest promotion
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(buf));
+        if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+      }
+      if (!ok) break;
+      const int64_t r = bi * BM + row_in_tile;
+      const bool row_ok = r < p.M;
+      double part = 0.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t c0 = bj * BN + half * 128 + c * 32;
+        float* v = &acc[c * 32];
+        if (!row_ok || c0 >= p.N) continue;
+        const bool full_chunk = c0 + 32 <= p.N;
+        if (EPI == TC_EPI_NS) {
+          float* xr = p.X + r * p.ldx + c0;
+          uint16_t* pr = p.out_planes + r * p.ldo + c0;
+          if (full_chunk) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float4 xo = *reinterpret_cast<const float4*>(xr + 4 * i);
+              v[4 * i + 0] = 1.5f * xo.x - 0.5f * v[4 * i + 0];
+              v[4 * i + 1] = 1.5f * xo.y - 0.5f * v[4 * i + 1];
+              v[4 * i + 2] = 1.5f * xo.z - 0.5f * v[4 * i + 2];
+              v[4 * i + 3] = 1.5f * xo.w - 0.5f * v[4 * i + 3];
+              *reinterpret_cast<float4*>(xr + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+            store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (c0 + j < p.N) {
+                float xn = 1.5f * xr[j] - 0.5f * v[j];
+                xr[j] = xn;
+                store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, xn);
+              }
+            }
+          }
+        } else if (EPI == TC_EPI_GRAM) {
+          uint16_t* pr = p.out_planes + r * p.ldo + c0;
+          float s_off = 0.f, s_diag = 0.f;
+          if (full_chunk && r < c0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
+            store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t cc = c0 + j;
+              if (cc < p.N && r <= cc) {
+                if (r == cc) {
+                  float d = v[j] - 1.0f;
+                  s_diag = fmaf(d, d, s_diag);
+                } else {
+                  s_off = fmaf(v[j], v[j], s_off);
+                }
+                store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
+              }
+            }
+          }
+          part += 2.0 * (double)s_off + (double)s_diag;
+        } else {  // STORE
+          float* cr = p.C + r * p.ldc + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (c0 + j < p.N && !(tri && r > c0 + j)) {
+              float o = p.alpha * v[j];
+              if (p.beta != 0.0f) o = fmaf(p.beta, cr[j], o);
+              cr[j] = o;
+            }
+          }
+        }
+      }
+      if (EPI == TC_EPI_GRAM) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if (lane == 0) p.partials[t * EPI_WARPS + (warp - 2)] = part;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
+    if (p.st) {
+      atomicOr(&p.st->err_flags, 1u);
+      p.st->status = ST_TIMEOUT;  // later launches of this solve return at once
+    } else {
+      atomicOr(&g_tc_error, 1u);
+    }
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 3-D map (columns, rows, planes) over an operand's planes; the box is one stage's slice.
+bool make_map(CUtensorMap* map, const TcOperand& op, int nplanes, bool mn_major, int mn_box) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)op.cols, (cuuint64_t)op.rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)op.plane_stride * 2};
+  cuuint32_t box[3];
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMapSwizzle swz;
+  if (mn_major) {
+    box[0] = 64; box[1] = BK; box[2] = (cuuint32_t)nplanes;
+    swz = CU_TENSOR_MAP_SWIZZLE_128B;
+  } else {
+    box[0] = BK; box[1] = (cuuint32_t)mn_box; box[2] = (cuuint32_t)nplanes;
+    swz = CU_TENSOR_MAP_SWIZZLE_64B;
+  }
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(op.planes), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <int P, bool A_MN, bool B_MN, int EPI>
+cudaError_t launch_t(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int64_t tm, int64_t tn,
+                     int64_t ntiles, cudaStream_t s) {
+  auto k = tc_gemm_kernel<P, A_MN, B_MN, EPI>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P>::SMEM);
+  if (e != cudaSuccess) return e;
+  int64_t grid = ntiles < sm_count() ? ntiles : sm_count();
+  k<<<(unsigned)grid, NTHREADS, Cfg<P>::SMEM, s>>>(ma, mb, a, tm, tn, ntiles);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t dispatch_p(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int64_t tm, int64_t tn,
+                       int64_t ntiles, cudaStream_t s) {
+  const bool amn = !a.a.kmajor, bmn = !a.b.kmajor;
+  switch (a.epi) {
+    case TC_EPI_NS:
+      if (!amn && bmn) return launch_t<P, false, true, TC_EPI_NS>(ma, mb, a, tm, tn, ntiles, s);
+      return cudaErrorInvalidValue;
+    case TC_EPI_GRAM:
+      if (amn && bmn) return launch_t<P, true, true, TC_EPI_GRAM>(ma, mb, a, tm, tn, ntiles, s);
+      return cudaErrorInvalidValue;
+    default:
+      if (amn && bmn) return launch_t<P, true, true, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
+      if (!amn && bmn) return launch_t<P, false, true, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
+      if (amn && !bmn) return launch_t<P, true, false, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
+      return launch_t<P, false, false, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
+  }
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+int tc_gram_partials(int64_t n) {
+  const int64_t tm = (n + BM - 1) / BM, tn = (n + BN - 1) / BN;
+  return (int)(tri_tiles(tm, tn) * EPI_WARPS);
+}
+
+cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s) {
+  if (a.nplanes < 1 || a.nplanes > 3 || a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaErrorInvalidValue;
+  const TcOperand* ops[2] = {&a.a, &a.b};
+  for (const TcOperand* o : ops)
+    if (!o->planes || !aligned(o->planes, 16) || o->ld % 8 || o->plane_stride % 8) return cudaErrorInvalidValue;
+  if (a.epi == TC_EPI_NS || a.epi == TC_EPI_GRAM) {
+    if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8) return cudaErrorInvalidValue;
+    if (a.out_nplanes < 1 || a.out_nplanes > 3) return cudaErrorInvalidValue;
+  }
+  if (a.epi == TC_EPI_NS && (!a.X || !aligned(a.X, 16) || a.ldx % 4)) return cudaErrorInvalidValue;
+  if (a.epi == TC_EPI_GRAM && !a.partials) return cudaErrorInvalidValue;
+  if (a.triangular && a.M != a.N) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.a, a.nplanes, !a.a.kmajor, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, a.b, a.nplanes, !a.b.kmajor, BN)) return cudaErrorInvalidValue;
+  const int64_t tm = (a.M + BM - 1) / BM, tn = (a.N + BN - 1) / BN;
+  const int64_t ntiles = a.triangular ? tri_tiles(tm, tn) : tm * tn;
+  switch (a.nplanes) {
+    case 1: return dispatch_p<1>(ma, mb, a, tm, tn, ntiles, s);
+    case 2: return dispatch_p<2>(ma, mb, a, tm, tn, ntiles, s);
+    default: return dispatch_p<3>(ma, mb, a, tm, tn, ntiles, s);
+  }
+}
+
 }  // namespace polar

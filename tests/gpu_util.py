@@ -25,15 +25,19 @@ def metrics(a, u, h, u_ref=None):
     return out
 
 
+# operand encoding error of a P-plane BF16 split product, relative to |a||b| per term:
+# P = 1 drops the rounding of both operands (2 * 2^-8 + 2^-16), P = 2 drops lo*lo and
+# the two 2^-16 remainders, P = 3 drops mid*lo, lo*mid, lo*lo (about 2^-23)
+ENC = {None: 0.0, 1: 2.01 * 2.0 ** -8, 2: 3.01 * 2.0 ** -16, 3: 2.01 * 2.0 ** -23}
+PASSES = {None: 1, 1: 1, 2: 3, 3: 6}
+
+
 def gemm_bound(a_abs, b_abs, k, c_abs=None, alpha=1.0, beta=0.0, planes=None):
-    """Elementwise bound |fl(alpha AB + beta C) - (alpha AB + beta C)| for float32 dot
-    products of length k accumulated with FMAs (gamma_k with u = 2^-24), plus the
-    operand encoding error of a P-plane BF16 split (2 * 2^(-8P) per product, P < 3)."""
+    """Elementwise bound on |fl(alpha AB + beta C) - (alpha AB + beta C)|: float32
+    accumulation of passes * k terms (gamma with u = 2^-24) plus the split's
+    encoding error, times |A||B|; beta C adds two roundings."""
     base = a_abs @ b_abs
-    u_enc = 0.0 if planes in (None, 3) else 2.0 * 2.0 ** (-8 * planes)
-    bound = abs(alpha) * ((k + 4) * U32 + u_enc) * base
-    if planes == 3:
-        bound = abs(alpha) * ((k + 8) * U32) * base
+    bound = abs(alpha) * ((PASSES[planes] * k + 4) * U32 + ENC[planes]) * base
     if c_abs is not None and beta != 0.0:
         bound = bound + 2 * U32 * abs(beta) * c_abs
     return bound + 1e-30

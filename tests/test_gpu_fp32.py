@@ -37,7 +37,11 @@ def test_split_bit_exact(lib, torch_cuda, planes):
     x[:8] = np.array([0.0, -0.0, 1.0, 3.4e38, -3.39e38, 1e-40, np.inf, -np.inf], dtype=np.float32)
     got = lib.polar_split_bf16(torch.from_numpy(x).cuda(), planes).cpu().numpy().view(np.uint16)
     want = np.stack(precision.split_planes(x, planes))
-    assert np.array_equal(got, want)
+    # a NaN plane (Inf - Inf in a remainder) is any NaN: its sign and payload are not defined
+    nan_w = ((want & 0x7F80) == 0x7F80) & ((want & 0x007F) != 0)
+    nan_g = ((got & 0x7F80) == 0x7F80) & ((got & 0x007F) != 0)
+    assert np.array_equal(nan_w, nan_g)
+    assert np.array_equal(got[~nan_w], want[~nan_w])
 
 
 SHAPES = [(1, 1, 1), (7, 5, 3), (129, 130, 131), (300, 257, 100), (64, 64, 1000), (200, 33, 517)]
