@@ -164,6 +164,27 @@ POLAR_API polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const flo
 POLAR_API polar_status_t polar_split_bf16(const float* X, int64_t count, int planes, uint16_t* out,
                                 polar_stream_t stream);
 
+/* Size of the static device array behind polar_gemm_noalloc (32 MiB). */
+#define POLAR_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* polar_gemm without any device allocation. The paper has no counterpart: this is a
+ * library-service entry point. polar_gemm keeps the BF16 planes of its operands in a
+ * scratch buffer it grows with cudaMalloc/cudaFree; callers that must not allocate
+ * (device memory owned entirely by another allocator, or a latency-critical loop that
+ * cannot take the synchronisation a cudaFree implies) use this variant, whose planes
+ * live in one static device array of POLAR_NOALLOC_SCRATCH_BYTES per GPU, held from
+ * the first use on that GPU until the process exits.
+ * Arguments, layouts and results are those of polar_gemm. The BF16 modes need
+ * prec_planes * (rows_A * round64(cols_A) + rows_B * round64(cols_B)) * 2 bytes of the
+ * array (stored shapes, rows rounded as listed); a larger problem returns POLAR_ENOMEM
+ * before any device work. FP32 needs no scratch. The first call on a device looks up the
+ * array's address there (cudaGetSymbolAddress with that device current), so make it
+ * before any stream capture. All calls share the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams or threads) race. */
+POLAR_API polar_status_t polar_gemm_noalloc(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                                            const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                                            float* C, int64_t ldc, int prec, polar_stream_t stream);
+
 /* Number of SMs and compute capability of the current device; ECUDA without one. */
 POLAR_API polar_status_t polar_device_query(int* sm_count, int* cc_major, int* cc_minor);
 

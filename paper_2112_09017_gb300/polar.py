@@ -75,6 +75,7 @@ def load():
         "polar_batched_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), f64, vp, vp, vp]),
         "polar_plan_destroy": (None, [vp]),
         "polar_gemm": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
+        "polar_gemm_noalloc": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
         "polar_syrk": (i32, [i64, i64, f32, vp, i64, f32, vp, i64, i32, vp]),
         "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
         "polar_device_query": (i32, [C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
@@ -186,6 +187,25 @@ def polar_gemm(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, prec
                           B.stride(0), float(beta), _ptr(C_), C_.stride(0), int(prec), _stream(stream))
     if r != POLAR_OK:
         raise PolarError(r, "polar_gemm")
+
+
+def polar_gemm_noalloc(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None,
+                       raw_status=False):
+    """polar_gemm with its split planes in the library's fixed static device array
+    (no device allocation); returns the status code when raw_status."""
+    _check_f32_2d(A, "A"); _check_f32_2d(B, "B"); _check_f32_2d(C_, "C")
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    N = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != K or tuple(C_.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    r = load().polar_gemm_noalloc(int(trans_a), int(trans_b), M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                                  B.stride(0), float(beta), _ptr(C_), C_.stride(0), int(prec), _stream(stream))
+    if raw_status:
+        return r
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_gemm_noalloc")
+    return r
 
 
 def polar_syrk(A, C_, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None):
