@@ -7,7 +7,9 @@
 //
 // Tile 128 x 128 x 16, 256 threads, 8 x 8 accumulators per thread in two
 // 4 x 4 quadrants (rows ty*4 and 64 + ty*4, columns tx*4 and 64 + tx*4), two
-// shared-memory buffers with register prefetch of the next k-slice.
+// shared-memory buffers with register prefetch of the next k-slice. Each
+// 16-wide k-slice is summed into a fresh register tile before it is added to
+// the running sums (blocked summation).
 #include "internal.cuh"
 
 namespace polar {
@@ -131,6 +133,13 @@ __global__ void __launch_bounds__(NT) simt_gemm_kernel(SimtArgs p, bool vec_a, b
       load_slice(p.A, p.lda, akm, m0, p.M, (kt + 1) * BK, p.K, vec_a, ra);
       load_slice(p.B, p.ldb, bkm, n0, p.N, (kt + 1) * BK, p.K, vec_b, rb);
     }
+    // each k-slice sums into a fresh tile first (blocked summation: the rounding
+    // error of the running sums grows with K / 16 additions, not K)
+    float part[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) part[i][j] = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float a[8], b[8];
@@ -145,8 +154,12 @@ __global__ void __launch_bounds__(NT) simt_gemm_kernel(SimtArgs p, bool vec_a, b
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) part[i][j] = fmaf(a[i], b[j], part[i][j]);
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] += part[i][j];
     if (kt + 1 < nk) {
       store_slice(sm.a[cur ^ 1], akm, ra);
       store_slice(sm.b[cur ^ 1], bkm, rb);

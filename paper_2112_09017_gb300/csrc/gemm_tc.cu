@@ -10,11 +10,11 @@
 //
 // The tensor cores add into their FP32 accumulator with round-toward-zero
 // (inside one MMA and across MMAs), so a long accumulation drifts toward zero
-// by about half an ulp per step. The kernel therefore accumulates each 32-wide
-// k-slice into a fresh TMEM buffer, issuing the small plane pairs first and
-// hi*hi last (the truncations of the small passes happen at 2^-8 of the
-// result's scale), and the epilogue warps add every slice into FP32 registers
-// with round-to-nearest ("promotion").
+// by about half an ulp per step. The kernel therefore accumulates each short
+// k-slice (64 of K for three planes) into a fresh TMEM buffer, issuing the
+// small plane pairs first and hi*hi last in every k-stage (the truncations of
+// the small passes happen at 2^-8 of the result's scale), and the epilogue warps
+// add every slice into FP32 registers with round-to-nearest ("promotion").
 //
 // Structure (one CTA per SM, persistent over output tiles of 128 x 256):
 //   warp 0      TMA producer: cp.async.bulk.tensor 3-D loads (columns, rows,
@@ -26,7 +26,8 @@
 //               tcgen05.ld of every slice, running sums in registers, then the
 //               fused output step of the tile:
 //                 STORE  C = alpha acc + beta C   (optionally upper triangle)
-//                 NS     X <- 1.5 X - 0.5 acc in place, plus its BF16 planes
+//                 NS     X_{k+1} = 1.5 X_k - 0.5 acc, X_k read from its three
+//                        BF16 planes (an exact FP32 encoding), written as planes
 //                 GRAM   BF16 planes of G (upper triangle) and float64
 //                        partials of ||G - I||_F^2 per tile and warp
 // Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-slices)
@@ -35,6 +36,8 @@
 // records an error flag, lets its copies and MMAs drain, frees TMEM and returns.
 #include <cuda.h>
 #include <math.h>
+
+#include <stdlib.h>
 
 #include <mutex>
 
@@ -151,23 +154,6 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -180,6 +166,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// acc[0..16) += the 16 values of a TMEM load, two lanes per packed add (round-to-nearest).
+__device__ __forceinline__ void add16_packed(float* acc, const float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    asm("{\n\t.reg .b64 a, b, c;\n\t"
+        "mov.b64 a, {%0, %1};\n\t"
+        "mov.b64 b, {%2, %3};\n\t"
+        "add.rn.f32x2 c, a, b;\n\t"
+        "mov.b64 {%0, %1}, c;\n\t}"
+        : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+        : "f"(v[2 * i]), "f"(v[2 * i + 1]));
+  }
 }
 
 // Shared-memory matrix descriptor for tcgen05.mma (version 1; no base offset).
@@ -202,11 +202,15 @@ __host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn) {
 
 // Plane pairs of the split product in issue order for `np` planes: the smallest
 // terms first, hi*hi last (6 passes: (1,1) (0,2) (2,0) (0,1) (1,0) (0,0)).
-__device__ __forceinline__ void pass_planes(int np, int i, int& pa, int& pb) {
-  const int first = np == 1 ? 5 : (np == 2 ? 3 : 0);
-  const int j = first + i;
-  pa = (j == 0) ? 1 : (j == 1) ? 0 : (j == 2) ? 2 : (j == 3) ? 0 : (j == 4) ? 1 : 0;
-  pb = (j == 0) ? 1 : (j == 1) ? 2 : (j == 2) ? 0 : (j == 3) ? 1 : (j == 4) ? 0 : 0;
+__host__ __device__ constexpr int pass_a(int np, int i) {
+  return ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 0 ? 1
+       : ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 2 ? 2
+       : ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 4 ? 1 : 0;
+}
+__host__ __device__ constexpr int pass_b(int np, int i) {
+  return ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 0 ? 1
+       : ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 1 ? 2
+       : ((np == 1 ? 5 : np == 2 ? 3 : 0) + i) == 3 ? 1 : 0;
 }
 
 __host__ __device__ __forceinline__ int passes_for(int planes) { return planes == 1 ? 1 : (planes == 2 ? 3 : 6); }
@@ -264,11 +268,240 @@ __device__ __forceinline__ void store_planes1(uint16_t* base, int64_t pstride, i
 }
 
 // ---------------------------------------------------------------- the kernel
+//
+// The three roles are separate non-inlined functions so that the register
+// pressure of the epilogue (128 running sums per thread) does not make the
+// single-thread producer and MMA loops spill: a spilled loop variable reloaded
+// from local memory (which mostly misses the small L1 left beside the stages)
+// stalls the thread that feeds the tensor pipe.
+
+struct Bars {
+  uint32_t full0, empty0, tfull0, tempty0, drain;  // shared addresses; stage s at + 8 s
+};
+
+template <int P, bool A_MN, bool B_MN>
+__device__ __noinline__ void role_producer(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t smem_base,
+                                           Bars br, volatile int* abort_flag, int64_t tm, int64_t tn,
+                                           int64_t ntiles, int64_t nk, bool tri) {
+  using C = Cfg<P>;
+  constexpr int S = C::STAGES;
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmA)) : "memory");
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmB)) : "memory");
+  int stage = 0;
+  uint32_t phase = 0;
+  uint32_t armed = 0, armed_phase = 0;  // bit s: stage s was armed / the parity it was armed with
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    int64_t bi, bj;
+    tile_coords(t, tm, tn, tri, bi, bj);
+    const int m0 = (int)(bi * BM), n0 = (int)(bj * BN);
+    for (int64_t kb = 0; kb < nk; ++kb) {
+      if (!mbar_wait(br.empty0 + 8 * stage, phase ^ 1u, abort_flag)) { ok = false; break; }
+      const uint32_t fb = br.full0 + 8 * stage;
+      mbar_expect_tx(fb, C::STAGE_BYTES);
+      armed |= 1u << stage;
+      armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
+      const uint32_t a_dst = smem_base + stage * C::STAGE_BYTES;
+      const uint32_t b_dst = a_dst + C::A_BYTES;
+      const int k0 = (int)(kb * BK);
+      if (A_MN) {
+#pragma unroll
+        for (int c = 0; c < BM / 64; ++c) tma_load_3d(a_dst + c * P * 4096, tmA, fb, m0 + 64 * c, k0, 0);
+      } else {
+        tma_load_3d(a_dst, tmA, fb, k0, m0, 0);
+      }
+      if (B_MN) {
+#pragma unroll
+        for (int c = 0; c < BN / 64; ++c) tma_load_3d(b_dst + c * P * 4096, tmB, fb, n0 + 64 * c, k0, 0);
+      } else {
+        tma_load_3d(b_dst, tmB, fb, k0, n0, 0);
+      }
+      if (++stage == S) { stage = 0; phase ^= 1u; }
+    }
+  }
+  // every copy this thread started lands before the CTA can exit
+  for (int s2 = 0; s2 < S; ++s2)
+    if (armed & (1u << s2)) mbar_drain(br.full0 + 8 * s2, (armed_phase >> s2) & 1u);
+}
+
+// The NP-plane passes on one k-stage: descriptors are the stage-0 bases plus
+// compile-time offsets (the start-address field is the low 14 bits, address / 16).
+template <int P, bool A_MN, bool B_MN, int NP>
+__device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t first_acc) {
+  constexpr uint32_t idesc = make_idesc(A_MN, B_MN);
+#pragma unroll
+  for (int ps = 0; ps < passes_for(NP); ++ps) {
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+      const uint32_t aoff = A_MN ? pass_a(NP, ps) * 4096 + kk * 2048 : pass_a(NP, ps) * A_PLANE + kk * 32;
+      const uint32_t boff = B_MN ? pass_b(NP, ps) * 4096 + kk * 2048 : pass_b(NP, ps) * B_PLANE + kk * 32;
+      tc_mma(d_tmem, a_desc + (aoff >> 4), b_desc + (boff >> 4), idesc, (ps == 0 && kk == 0) ? first_acc : 1u);
+    }
+  }
+}
+
+template <int P, bool A_MN, bool B_MN>
+__device__ __noinline__ void role_mma(uint32_t smem_base, uint32_t tmem_base, Bars br, volatile int* abort_flag,
+                                      int64_t ntiles, int64_t nk, int SL, int pu) {
+  using C = Cfg<P>;
+  constexpr int S = C::STAGES;
+  const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * 4096, 1024, 2) : smem_desc(smem_base, 16, 512, 4);
+  const uint64_t b_desc0 = B_MN ? smem_desc(smem_base + C::A_BYTES, P * 4096, 1024, 2)
+                                : smem_desc(smem_base + C::A_BYTES, 16, 512, 4);
+  int stage = 0;
+  uint32_t phase = 0;
+  int buf = 0;
+  uint32_t buf_phase = 0;
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    int kin = 0;  // k-stage index within the current slice
+    for (int64_t kb = 0; kb < nk; ++kb) {
+      // SL k-stages into a fresh slice buffer, then published to the epilogue
+      const bool slice_start = kin == 0;
+      const bool slice_end = kin == SL - 1 || kb == nk - 1;
+      if (slice_start && !mbar_wait(br.tempty0 + 8 * buf, buf_phase ^ 1u, abort_flag)) { ok = false; break; }
+      if (!mbar_wait(br.full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+      const uint64_t soff = (uint64_t)((stage * C::STAGE_BYTES) >> 4);
+      const uint32_t first_acc = slice_start ? 0u : 1u;
+      if (pu == P) issue_stage<P, A_MN, B_MN, P>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      else if (pu == 2) issue_stage<P, A_MN, B_MN, (P >= 2 ? 2 : P)>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      else issue_stage<P, A_MN, B_MN, 1>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      tc_commit(br.empty0 + 8 * stage);
+      if (slice_end) {
+        tc_commit(br.tfull0 + 8 * buf);
+        if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+        kin = 0;
+      } else {
+        ++kin;
+      }
+      if (++stage == S) { stage = 0; phase ^= 1u; }
+    }
+  }
+  // every MMA issued so far completes before TMEM is released
+  tc_commit(br.drain);
+  mbar_drain(br.drain, 0);
+}
+
+template <int EPI>
+__device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, Bars br, volatile int* abort_flag,
+                                           int64_t tm, int64_t tn, int64_t ntiles, int64_t nslices, bool tri,
+                                           int warp, int lane) {
+  const int q = warp & 3;                  // TMEM lane quarter this warp may access
+  const int half = (warp - 2) >> 2;        // which 128 of the tile's 256 columns
+  const int row_in_tile = q * 32 + lane;
+  const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
+  int buf = 0;
+  uint32_t buf_phase = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t bi, bj;
+    tile_coords(t, tm, tn, tri, bi, bj);
+    float acc[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+    bool ok = true;
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+      if (!mbar_wait(br.tfull0 + 8 * buf, buf_phase, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float v[16];
+        tmem_ld16(t_lane + (uint32_t)(buf * BN + c * 16), v);
+        add16_packed(&acc[c * 16], v);   // round-to-nearest promotion
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(br.tempty0 + 8 * buf);
+      if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+    }
+    if (!ok) return;
+    const int64_t r = bi * BM + row_in_tile;
+    const bool row_ok = r < p.M;
+    double part = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t c0 = bj * BN + half * 128 + c * 32;
+      float* v = &acc[c * 32];
+      if (!row_ok || c0 >= p.N) continue;
+      const bool full_chunk = c0 + 32 <= p.N;
+      if (EPI == TC_EPI_NS) {
+        // X_{k+1} = 1.5 X_k - 0.5 X_k G: X_k from its three planes (exact), result as planes
+        const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
+        uint16_t* pr = p.out_planes + r * p.ldo + c0;
+        if (full_chunk) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint4 h = *reinterpret_cast<const uint4*>(xr + 8 * i);
+            uint4 m = *reinterpret_cast<const uint4*>(xr + p.x_plane_stride + 8 * i);
+            uint4 l = *reinterpret_cast<const uint4*>(xr + 2 * p.x_plane_stride + 8 * i);
+            const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, mw[4] = {m.x, m.y, m.z, m.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int w = e >> 1, sh = (e & 1) * 16;
+              const float x = (bf16_to_f32_dev((uint16_t)(hw[w] >> sh)) + bf16_to_f32_dev((uint16_t)(mw[w] >> sh))) +
+                              bf16_to_f32_dev((uint16_t)(lw[w] >> sh));
+              v[8 * i + e] = 1.5f * x - 0.5f * v[8 * i + e];
+            }
+          }
+          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (c0 + j < p.N) {
+              const float x = (bf16_to_f32_dev(xr[j]) + bf16_to_f32_dev(xr[p.x_plane_stride + j])) +
+                              bf16_to_f32_dev(xr[2 * p.x_plane_stride + j]);
+              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, 1.5f * x - 0.5f * v[j]);
+            }
+          }
+        }
+      } else if (EPI == TC_EPI_GRAM) {
+        uint16_t* pr = p.out_planes + r * p.ldo + c0;
+        float s_off = 0.f, s_diag = 0.f;
+        if (full_chunk && r < c0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
+          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t cc = c0 + j;
+            if (cc < p.N && r <= cc) {
+              if (r == cc) {
+                float d = v[j] - 1.0f;
+                s_diag = fmaf(d, d, s_diag);
+              } else {
+                s_off = fmaf(v[j], v[j], s_off);
+              }
+              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
+            }
+          }
+        }
+        part += 2.0 * (double)s_off + (double)s_diag;
+      } else {  // STORE
+        float* cr = p.C + r * p.ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (c0 + j < p.N && !(tri && r > c0 + j)) {
+            float o = p.alpha * v[j];
+            if (p.beta != 0.0f) o = fmaf(p.beta, cr[j], o);
+            cr[j] = o;
+          }
+        }
+      }
+    }
+    if (EPI == TC_EPI_GRAM) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      if (lane == 0) p.partials[t * EPI_WARPS + (warp - 2)] = part;
+    }
+  }
+}
 
 template <int P, bool A_MN, bool B_MN, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs p,
-                   int64_t tm, int64_t tn, int64_t ntiles) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ TcArgs p, int64_t tm, int64_t tn, int64_t ntiles) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
   if (p.st && p.st->status != ST_RUNNING) return;
@@ -279,23 +512,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const uint32_t smem_base = smem_u32(smem);
-  auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
-  auto empty_bar = [&](int s) { return smem_u32(&bars[S + s]); };
-  auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * S + a]); };
-  auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * S + 2 + a]); };
-  const uint32_t drain_bar = smem_u32(&bars[2 * S + 4]);
+  Bars br;
+  br.full0 = smem_u32(&bars[0]);
+  br.empty0 = smem_u32(&bars[S]);
+  br.tfull0 = smem_u32(&bars[2 * S]);
+  br.tempty0 = smem_u32(&bars[2 * S + 2]);
+  br.drain = smem_u32(&bars[2 * S + 4]);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(br.full0 + 8 * s, 1);
+      mbar_init(br.empty0 + 8 * s, 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), EPI_WARPS);
+      mbar_init(br.tfull0 + 8 * a, 1);
+      mbar_init(br.tempty0 + 8 * a, EPI_WARPS);
     }
-    mbar_init(drain_bar, 1);
+    mbar_init(br.drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -312,198 +546,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   const bool tri = p.triangular != 0;
   const int64_t nk = (p.K + BK - 1) / BK;
+  const int SL = p.slice_stages > 0 ? p.slice_stages : 1;   // k-stages per promoted slice
+  const int64_t nslices = (nk + SL - 1) / SL;
 
   if (warp == 0) {
-    // ------------------------------------------------ TMA producer
-    if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-      int stage = 0;
-      uint32_t phase = 0;
-      int armed[S];
-#pragma unroll
-      for (int s = 0; s < S; ++s) armed[s] = -1;
-      bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        int64_t bi, bj;
-        tile_coords(t, tm, tn, tri, bi, bj);
-        const int m0 = (int)(bi * BM), n0 = (int)(bj * BN);
-        for (int64_t kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
-          const uint32_t fb = full_bar(stage);
-          mbar_expect_tx(fb, C::STAGE_BYTES);
-          armed[stage] = (int)phase;
-          const uint32_t a_dst = smem_base + stage * C::STAGE_BYTES;
-          const uint32_t b_dst = a_dst + C::A_BYTES;
-          const int k0 = (int)(kb * BK);
-          if (A_MN) {
-#pragma unroll
-            for (int c = 0; c < BM / 64; ++c) tma_load_3d(a_dst + c * P * 4096, &tmA, fb, m0 + 64 * c, k0, 0);
-          } else {
-            tma_load_3d(a_dst, &tmA, fb, k0, m0, 0);
-          }
-          if (B_MN) {
-#pragma unroll
-            for (int c = 0; c < BN / 64; ++c) tma_load_3d(b_dst + c * P * 4096, &tmB, fb, n0 + 64 * c, k0, 0);
-          } else {
-            tma_load_3d(b_dst, &tmB, fb, k0, n0, 0);
-          }
-          if (++stage == S) { stage = 0; phase ^= 1u; }
-        }
-      }
-      // let every copy this thread started land before the CTA can exit
-#pragma unroll
-      for (int s = 0; s < S; ++s)
-        if (armed[s] >= 0) mbar_drain(full_bar(s), (uint32_t)armed[s]);
-    }
+    if (lane == 0) role_producer<P, A_MN, B_MN>(&tmA, &tmB, smem_base, br, abort_flag, tm, tn, ntiles, nk, tri);
   } else if (warp == 1) {
-    // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       const int pu = p.planes_dyn ? min(max(*p.planes_dyn, 1), P) : P;
-      const int npass = passes_for(pu);
-      constexpr uint32_t idesc = make_idesc(A_MN, B_MN);
-      int stage = 0;
-      uint32_t phase = 0;
-      int buf = 0;
-      uint32_t buf_phase = 0;
-      bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        for (int64_t kb = 0; kb < nk; ++kb) {
-          // one k-slice into a fresh slice buffer, published to the epilogue
-          if (!mbar_wait(tempty_bar(buf), buf_phase ^ 1u, abort_flag)) { ok = false; break; }
-          if (!mbar_wait(full_bar(stage), phase, abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-          const uint32_t a_st = smem_base + stage * C::STAGE_BYTES;
-          const uint32_t b_st = a_st + C::A_BYTES;
-          for (int ps = 0; ps < npass; ++ps) {
-            int pa, pb;
-            pass_planes(pu, ps, pa, pb);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              uint64_t ad, bd;
-              if (A_MN) ad = smem_desc(a_st + pa * 4096 + kk * 2048, P * 4096, 1024, 2);
-              else      ad = smem_desc(a_st + pa * A_PLANE + kk * 32, 16, 512, 4);
-              if (B_MN) bd = smem_desc(b_st + pb * 4096 + kk * 2048, P * 4096, 1024, 2);
-              else      bd = smem_desc(b_st + pb * B_PLANE + kk * 32, 16, 512, 4);
-              tc_mma(d_tmem, ad, bd, idesc, (ps > 0 || kk > 0) ? 1u : 0u);
-            }
-          }
-          tc_commit(empty_bar(stage));
-          tc_commit(tfull_bar(buf));
-          if (++stage == S) { stage = 0; phase ^= 1u; }
-          if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
-        }
-      }
-      // every MMA issued so far completes before TMEM is released
-      tc_commit(drain_bar);
-      mbar_drain(drain_bar, 0);
+      role_mma<P, A_MN, B_MN>(smem_base, tmem_base, br, abort_flag, ntiles, nk, SL, pu);
     }
   } else {
-    // ------------------------------------------------ epilogue (warps 2..9)
-    const int q = warp & 3;                  // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;        // which 128 of the tile's 256 columns
-    const int row_in_tile = q * 32 + lane;
-    const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
-    int buf = 0;
-    uint32_t buf_phase = 0;
-    bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int64_t bi, bj;
-      tile_coords(t, tm, tn, tri, bi, bj);
-      float acc[128];
-#pragma unroll
-      for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
-      for (int64_t kb = 0; kb < nk; ++kb) {
-        if (!mbar_wait(tfull_bar(buf), buf_phase, abort_flag)) { ok = false; break; }
-        tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          float v[16];
-          tmem_ld16(t_lane + (uint32_t)(buf * BN + c * 16), v);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[c * 16 + j] += v[j];   // round-to-nearest promotion
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(buf));
-        if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
-      }
-      if (!ok) break;
-      const int64_t r = bi * BM + row_in_tile;
-      const bool row_ok = r < p.M;
-      double part = 0.0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int64_t c0 = bj * BN + half * 128 + c * 32;
-        float* v = &acc[c * 32];
-        if (!row_ok || c0 >= p.N) continue;
-        const bool full_chunk = c0 + 32 <= p.N;
-        if (EPI == TC_EPI_NS) {
-          float* xr = p.X + r * p.ldx + c0;
-          uint16_t* pr = p.out_planes + r * p.ldo + c0;
-          if (full_chunk) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              float4 xo = *reinterpret_cast<const float4*>(xr + 4 * i);
-              v[4 * i + 0] = 1.5f * xo.x - 0.5f * v[4 * i + 0];
-              v[4 * i + 1] = 1.5f * xo.y - 0.5f * v[4 * i + 1];
-              v[4 * i + 2] = 1.5f * xo.z - 0.5f * v[4 * i + 2];
-              v[4 * i + 3] = 1.5f * xo.w - 0.5f * v[4 * i + 3];
-              *reinterpret_cast<float4*>(xr + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            }
-            store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (c0 + j < p.N) {
-                float xn = 1.5f * xr[j] - 0.5f * v[j];
-                xr[j] = xn;
-                store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, xn);
-              }
-            }
-          }
-        } else if (EPI == TC_EPI_GRAM) {
-          uint16_t* pr = p.out_planes + r * p.ldo + c0;
-          float s_off = 0.f, s_diag = 0.f;
-          if (full_chunk && r < c0) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
-            store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t cc = c0 + j;
-              if (cc < p.N && r <= cc) {
-                if (r == cc) {
-                  float d = v[j] - 1.0f;
-                  s_diag = fmaf(d, d, s_diag);
-                } else {
-                  s_off = fmaf(v[j], v[j], s_off);
-                }
-                store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
-              }
-            }
-          }
-          part += 2.0 * (double)s_off + (double)s_diag;
-        } else {  // STORE
-          float* cr = p.C + r * p.ldc + c0;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (c0 + j < p.N && !(tri && r > c0 + j)) {
-              float o = p.alpha * v[j];
-              if (p.beta != 0.0f) o = fmaf(p.beta, cr[j], o);
-              cr[j] = o;
-            }
-          }
-        }
-      }
-      if (EPI == TC_EPI_GRAM) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-        if (lane == 0) p.partials[t * EPI_WARPS + (warp - 2)] = part;
-      }
-    }
+    role_epilogue<EPI>(p, tmem_base, br, abort_flag, tm, tn, ntiles, nslices, tri, warp, lane);
   }
 
   tc_fence_before();
@@ -621,7 +675,24 @@ int tc_gram_partials(int64_t n) {
   return (int)(tri_tiles(tm, tn) * EPI_WARPS);
 }
 
-cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s) {
+// k-stages per promoted slice. Each slice accumulates 2 x passes MMAs per stage
+// with round-toward-zero before its round-to-nearest promotion; 24 MMAs per slice
+// for 3 and 2 planes (64 and 128 of K) and 16 for one plane (256 of K) keep the
+// promotion work below the MMA time of a slice. POLAR_TC_SLICE_STAGES (1..16)
+// overrides it for tuning.
+int default_slice_stages(int planes) {
+  static int env = [] {
+    const char* e = getenv("POLAR_TC_SLICE_STAGES");
+    int x = e ? atoi(e) : 0;
+    return (x >= 1 && x <= 16) ? x : 0;
+  }();
+  if (env) return env;
+  return planes == 3 ? 2 : planes == 2 ? 4 : 8;
+}
+
+cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
+  TcArgs a = a_in;
+  if (a.slice_stages <= 0) a.slice_stages = default_slice_stages(a.nplanes);
   if (a.nplanes < 1 || a.nplanes > 3 || a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaErrorInvalidValue;
   const TcOperand* ops[2] = {&a.a, &a.b};
   for (const TcOperand* o : ops)
@@ -630,8 +701,10 @@ cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s) {
     if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8) return cudaErrorInvalidValue;
     if (a.out_nplanes < 1 || a.out_nplanes > 3) return cudaErrorInvalidValue;
   }
-  if (a.epi == TC_EPI_NS && (!a.X || !aligned(a.X, 16) || a.ldx % 4)) return cudaErrorInvalidValue;
   if (a.epi == TC_EPI_GRAM && !a.partials) return cudaErrorInvalidValue;
+  if (a.epi == TC_EPI_NS &&
+      (!a.x_planes || !aligned(a.x_planes, 16) || a.ldxp % 8 || a.x_plane_stride % 8 || a.out_nplanes != 3))
+    return cudaErrorInvalidValue;
   if (a.triangular && a.M != a.N) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, a.a, a.nplanes, !a.a.kmajor, BM)) return cudaErrorInvalidValue;

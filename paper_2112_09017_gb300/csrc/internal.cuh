@@ -71,6 +71,9 @@ cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride,
 cudaError_t launch_copy2d(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t m, int64_t n,
                           cudaStream_t s);
 cudaError_t launch_split_flat(const float* x, int64_t count, int nplanes, uint16_t* out, cudaStream_t s);
+// dst = plane_0 + plane_1 + plane_2 (the FP32 value the three BF16 planes encode exactly)
+cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
+                                 float* dst, int64_t ldd, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // SIMT float32 GEMM / SYRK (gemm_simt.cu)
@@ -109,10 +112,11 @@ struct TcArgs {
   int epi;                 // TcEpi
   int triangular;          // SYRK upper-triangle tiles + mirror store
   float* C; int64_t ldc; float alpha, beta;      // STORE
-  float* X; int64_t ldx;                          // NS: X <- 1.5 X - 0.5 acc in place
+  const uint16_t* x_planes; int64_t ldxp; int64_t x_plane_stride;  // NS: three planes of X_k
   uint16_t* out_planes; int64_t ldo; int64_t out_plane_stride; int out_nplanes; // NS/GRAM plane output
   double* partials;                               // GRAM residual partials
   DevState* st;                                   // skip when not RUNNING; error flags
+  int slice_stages;                               // k-stages per promoted slice (0: library default)
   const int* planes_dyn;                          // if non-null: passes use min(*planes_dyn, nplanes)
                                                   // planes (schedules); outputs keep out_nplanes
 };

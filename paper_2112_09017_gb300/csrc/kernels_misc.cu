@@ -222,6 +222,17 @@ __global__ void mirror_kernel(T* __restrict__ C, int64_t ldc, int64_t plane_stri
   }
 }
 
+// Three BF16 planes that came from an FP32 value sum back to it exactly:
+// hi + mid has at most 16 significant bits and (hi + mid) + lo at most 24.
+__global__ void planes_to_f32_kernel(const uint16_t* __restrict__ P, int64_t ldp, int64_t ps, int64_t m, int64_t n,
+                                     float* __restrict__ dst, int64_t ldd) {
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      const int64_t i = r * ldp + c;
+      dst[r * ldd + c] = (bf16_bits_to_float(P[i]) + bf16_bits_to_float(P[ps + i])) + bf16_bits_to_float(P[2 * ps + i]);
+    }
+}
+
 __global__ void copy2d_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
                               int64_t m, int64_t n) {
   for (int64_t r = blockIdx.x; r < m; r += gridDim.x)
@@ -302,6 +313,12 @@ cudaError_t launch_mirror_f32(float* C, int64_t ldc, int64_t n, const DevState* 
 cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride, int nplanes, int64_t n,
                                  const DevState* st, const int* planes_dyn, cudaStream_t s) {
   mirror_kernel<uint16_t><<<mirror_blocks(n), kThreads, 0, s>>>(P, ldp, plane_stride, nplanes, n, st, planes_dyn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
+                                 float* dst, int64_t ldd, cudaStream_t s) {
+  planes_to_f32_kernel<<<grid_rows(m), kThreads, 0, s>>>(planes, ldp, plane_stride, m, n, dst, ldd);
   return cudaGetLastError();
 }
 

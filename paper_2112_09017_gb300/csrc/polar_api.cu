@@ -25,6 +25,8 @@ namespace {
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+constexpr int kStoredPlanes = 3;  // BF16 planes kept for X and G' on the tensor-core path
+
 int planes_of(int prec) {
   switch (prec) {
     case POLAR_BF16X6: return 3;
@@ -226,18 +228,18 @@ polar_status_t plan_setup(polar_plan_s* p) {
       p->X[i] = (float*)v;
     }
   } else {
-    if ((r = plan_alloc(p, (size_t)m * p->ldx * 4, &v)) != POLAR_OK) return r;
-    p->X[0] = (float*)v;
+    // X and G are kept only as three BF16 planes (an exact FP32 encoding); the
+    // products read the first P of them. Pitch padding is zeroed once.
     p->ldp = round_up(n, 64);
     p->xps = round_up(m * p->ldp, 64);
     p->gps = round_up(n * p->ldp, 64);
     for (int i = 0; i < 2; ++i) {
-      if ((r = plan_alloc(p, (size_t)p->P * p->xps * 2, &v)) != POLAR_OK) return r;
-      CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));  // zero pitch padding once
+      if ((r = plan_alloc(p, (size_t)kStoredPlanes * p->xps * 2, &v)) != POLAR_OK) return r;
+      CK(cudaMemset(v, 0, (size_t)kStoredPlanes * p->xps * 2));
       p->Xp[i] = (uint16_t*)v;
     }
-    if ((r = plan_alloc(p, (size_t)p->P * p->gps * 2, &v)) != POLAR_OK) return r;
-    CK(cudaMemset(v, 0, (size_t)p->P * p->gps * 2));
+    if ((r = plan_alloc(p, (size_t)kStoredPlanes * p->gps * 2, &v)) != POLAR_OK) return r;
+    CK(cudaMemset(v, 0, (size_t)kStoredPlanes * p->gps * 2));
     p->Gp = (uint16_t*)v;
     if ((r = plan_alloc(p, (size_t)p->P * p->xps * 2, &v)) != POLAR_OK) return r;
     CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));
@@ -354,7 +356,7 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
   g.b = g.a;
   g.nplanes = p->P;
   g.epi = TC_EPI_GRAM; g.triangular = 1;
-  g.out_planes = p->Gp; g.ldo = p->ldp; g.out_plane_stride = p->gps; g.out_nplanes = p->P;
+  g.out_planes = p->Gp; g.ldo = p->ldp; g.out_plane_stride = p->gps; g.out_nplanes = kStoredPlanes;
   g.partials = p->partials; g.st = p->st;
   g.planes_dyn = rule.sched ? &p->st->planes_next : nullptr;
   int pi;
@@ -367,7 +369,7 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
   // the finalize records the planes this Gram used (schedules: read on the device)
   e = launch_residual_finalize(p->partials, tc_gram_partials(p->n), p->st, rule, k, rule.sched ? -1 : p->P, s);
   if (e != cudaSuccess) return e;
-  return launch_mirror_planes(p->Gp, p->ldp, p->gps, p->P, p->n, p->st, nullptr, s);
+  return launch_mirror_planes(p->Gp, p->ldp, p->gps, kStoredPlanes, p->n, p->st, nullptr, s);
 }
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
@@ -377,8 +379,8 @@ cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cuda
   u.b = op_planes(p->Gp, p->n, p->n, p->ldp, p->gps, 0);
   u.nplanes = p->P;
   u.epi = TC_EPI_NS;
-  u.X = p->X[0]; u.ldx = p->ldx;
-  u.out_planes = p->Xp[(k + 1) & 1]; u.ldo = p->ldp; u.out_plane_stride = p->xps; u.out_nplanes = p->P;
+  u.x_planes = p->Xp[k & 1]; u.ldxp = p->ldp; u.x_plane_stride = p->xps;
+  u.out_planes = p->Xp[(k + 1) & 1]; u.ldo = p->ldp; u.out_plane_stride = p->xps; u.out_nplanes = kStoredPlanes;
   u.st = p->st;
   u.planes_dyn = rule.sched ? &p->st->planes_next : nullptr;
   int pi;
@@ -405,7 +407,7 @@ polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U
   if (p->P == 0)
     CK(launch_scale_split(A, lda, m, n, p->st, true, p->X[0], p->ldx, nullptr, 0, 0, 0, s));
   else
-    CK(launch_scale_split(A, lda, m, n, p->st, true, p->X[0], p->ldx, p->Xp[0], p->ldp, p->xps, p->P, s));
+    CK(launch_scale_split(A, lda, m, n, p->st, true, nullptr, 0, p->Xp[0], p->ldp, p->xps, kStoredPlanes, s));
   p->launches += 3;
 
   // Iterations in chunks; two chunks in flight so the device never waits on the host.
@@ -467,7 +469,7 @@ polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U
     CK(launch_simt_gemm(c, SIMT_EPI_STORE, s));
     p->launches += 2;
   } else {
-    CK(launch_copy2d(p->X[0], p->ldx, U, ldu, m, n, s));
+    CK(launch_planes_to_f32(p->Xp[it & 1], p->ldp, p->xps, m, n, U, ldu, s));
     CK(launch_scale_split(A, lda, m, n, nullptr, false, nullptr, 0, p->Ap, p->ldp, p->xps, p->P, s));
     TcArgs c{};
     c.M = n; c.N = n; c.K = m;
