@@ -28,7 +28,8 @@
 //                 STORE  C = alpha acc + beta C   (optionally upper triangle)
 //                 NS     X_{k+1} = 1.5 X_k - 0.5 acc, X_k read from its three
 //                        BF16 planes (an exact FP32 encoding), written as planes
-//                 GRAM   BF16 planes of G (upper triangle) and float64
+//                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
+//                        also stored at its mirror position) and float64
 //                        partials of ||G - I||_F^2 per tile and warp
 // Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-slices)
 // or MN-major (stored K x MN, 128-byte swizzle, 64-element MN chunks).
@@ -261,6 +262,33 @@ __device__ __forceinline__ void store_planes32(uint16_t* base, int64_t pstride, 
   }
 }
 
+// As store_planes32, and also the mirrored entries: value j goes to row (c0 + j),
+// column r of every plane (lanes hold consecutive r, so each store is 64 contiguous bytes).
+__device__ __forceinline__ void store_planes32_mirror(uint16_t* base, uint16_t* tbase, int64_t ld, int64_t pstride,
+                                                      int np, const float* x) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    uint32_t w[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint16_t a[3], b[3];
+      split_planes_dev<3>(x[8 * v + 2 * i], a);
+      split_planes_dev<3>(x[8 * v + 2 * i + 1], b);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        w[q][i] = (uint32_t)a[q] | ((uint32_t)b[q] << 16);
+        if (q < np) {
+          tbase[q * pstride + (int64_t)(8 * v + 2 * i) * ld] = a[q];
+          tbase[q * pstride + (int64_t)(8 * v + 2 * i + 1) * ld] = b[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (q < np) reinterpret_cast<uint4*>(base + q * pstride)[v] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+}
+
 __device__ __forceinline__ void store_planes1(uint16_t* base, int64_t pstride, int np, float x) {
   uint16_t a[3];
   split_planes_dev<3>(x, a);
@@ -279,23 +307,74 @@ struct Bars {
   uint32_t full0, empty0, tfull0, tempty0, drain;  // shared addresses; stage s at + 8 s
 };
 
-template <int P, bool A_MN, bool B_MN>
-__device__ __noinline__ void role_producer(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t smem_base,
-                                           Bars br, volatile int* abort_flag, int64_t tm, int64_t tn,
-                                           int64_t ntiles, int64_t nk, bool tri) {
+// What one output tile needs: its operand maps, origin, K-stage count, the
+// epilogue arguments of its problem and the index of its residual partials.
+struct TileCtx {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  int64_t bi, bj, nk;
+  const TcArgs* args;
+  int64_t part;  // partials slot base: tile index within its problem x EPI_WARPS
+};
+
+// One problem: tiles enumerated by tile_coords.
+struct SingleSrc {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  const TcArgs* args;
+  int64_t tm, tn, ntiles, nk;
+  bool tri;
+  __device__ __forceinline__ bool get(int64_t t, TileCtx& c) const {
+    tile_coords(t, tm, tn, tri, c.bi, c.bj);
+    c.ma = ma;
+    c.mb = mb;
+    c.nk = nk;
+    c.args = args;
+    c.part = t * EPI_WARPS;
+    return true;
+  }
+};
+
+// Many problems: tiles from a table; tiles of stopped problems are skipped (every
+// role reads the same status, which no launch-concurrent code changes).
+struct GroupSrc {
+  const TcTile* tiles;
+  const TcGroupEntry* entries;
+  int64_t ntiles;
+  __device__ __forceinline__ bool get(int64_t t, TileCtx& c) const {
+    const TcTile d = tiles[t];
+    const TcGroupEntry* e = entries + d.prob;
+    if (e->args.st && e->args.st->status != ST_RUNNING) return false;
+    c.ma = reinterpret_cast<const CUtensorMap*>(e->map_a);
+    c.mb = reinterpret_cast<const CUtensorMap*>(e->map_b);
+    c.bi = d.bi;
+    c.bj = d.bj;
+    c.nk = (e->args.K + BK - 1) / BK;
+    c.args = &e->args;
+    c.part = (int64_t)d.local * EPI_WARPS;
+    return true;
+  }
+};
+
+template <int P, bool A_MN, bool B_MN, class Src>
+__device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, Bars br, volatile int* abort_flag) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmA)) : "memory");
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmB)) : "memory");
   int stage = 0;
   uint32_t phase = 0;
   uint32_t armed = 0, armed_phase = 0;  // bit s: stage s was armed / the parity it was armed with
   bool ok = true;
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    int64_t bi, bj;
-    tile_coords(t, tm, tn, tri, bi, bj);
-    const int m0 = (int)(bi * BM), n0 = (int)(bj * BN);
-    for (int64_t kb = 0; kb < nk; ++kb) {
+  const CUtensorMap* last_a = nullptr;
+  for (int64_t t = blockIdx.x; t < src.ntiles && ok; t += gridDim.x) {
+    TileCtx c;
+    if (!src.get(t, c)) continue;
+    if (c.ma != last_a) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(c.ma)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(c.mb)) : "memory");
+      last_a = c.ma;
+    }
+    const int m0 = (int)(c.bi * BM), n0 = (int)(c.bj * BN);
+    for (int64_t kb = 0; kb < c.nk; ++kb) {
       if (!mbar_wait(br.empty0 + 8 * stage, phase ^ 1u, abort_flag)) { ok = false; break; }
       const uint32_t fb = br.full0 + 8 * stage;
       mbar_expect_tx(fb, C::STAGE_BYTES);
@@ -306,15 +385,15 @@ __device__ __noinline__ void role_producer(const CUtensorMap* tmA, const CUtenso
       const int k0 = (int)(kb * BK);
       if (A_MN) {
 #pragma unroll
-        for (int c = 0; c < BM / 64; ++c) tma_load_3d(a_dst + c * P * 4096, tmA, fb, m0 + 64 * c, k0, 0);
+        for (int cc = 0; cc < BM / 64; ++cc) tma_load_3d(a_dst + cc * P * 4096, c.ma, fb, m0 + 64 * cc, k0, 0);
       } else {
-        tma_load_3d(a_dst, tmA, fb, k0, m0, 0);
+        tma_load_3d(a_dst, c.ma, fb, k0, m0, 0);
       }
       if (B_MN) {
 #pragma unroll
-        for (int c = 0; c < BN / 64; ++c) tma_load_3d(b_dst + c * P * 4096, tmB, fb, n0 + 64 * c, k0, 0);
+        for (int cc = 0; cc < BN / 64; ++cc) tma_load_3d(b_dst + cc * P * 4096, c.mb, fb, n0 + 64 * cc, k0, 0);
       } else {
-        tma_load_3d(b_dst, tmB, fb, k0, n0, 0);
+        tma_load_3d(b_dst, c.mb, fb, k0, n0, 0);
       }
       if (++stage == S) { stage = 0; phase ^= 1u; }
     }
@@ -340,9 +419,9 @@ __device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, ui
   }
 }
 
-template <int P, bool A_MN, bool B_MN>
-__device__ __noinline__ void role_mma(uint32_t smem_base, uint32_t tmem_base, Bars br, volatile int* abort_flag,
-                                      int64_t ntiles, int64_t nk, int SL, int pu) {
+template <int P, bool A_MN, bool B_MN, class Src>
+__device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32_t tmem_base, Bars br,
+                                      volatile int* abort_flag, int SL, int pu) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
   const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * 4096, 1024, 2) : smem_desc(smem_base, 16, 512, 4);
@@ -353,12 +432,14 @@ __device__ __noinline__ void role_mma(uint32_t smem_base, uint32_t tmem_base, Ba
   int buf = 0;
   uint32_t buf_phase = 0;
   bool ok = true;
-  for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+  for (int64_t t = blockIdx.x; t < src.ntiles && ok; t += gridDim.x) {
+    TileCtx c;
+    if (!src.get(t, c)) continue;
     int kin = 0;  // k-stage index within the current slice
-    for (int64_t kb = 0; kb < nk; ++kb) {
+    for (int64_t kb = 0; kb < c.nk; ++kb) {
       // SL k-stages into a fresh slice buffer, then published to the epilogue
       const bool slice_start = kin == 0;
-      const bool slice_end = kin == SL - 1 || kb == nk - 1;
+      const bool slice_end = kin == SL - 1 || kb == c.nk - 1;
       if (slice_start && !mbar_wait(br.tempty0 + 8 * buf, buf_phase ^ 1u, abort_flag)) { ok = false; break; }
       if (!mbar_wait(br.full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
       tc_fence_after();
@@ -384,19 +465,20 @@ __device__ __noinline__ void role_mma(uint32_t smem_base, uint32_t tmem_base, Ba
   mbar_drain(br.drain, 0);
 }
 
-template <int EPI>
-__device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, Bars br, volatile int* abort_flag,
-                                           int64_t tm, int64_t tn, int64_t ntiles, int64_t nslices, bool tri,
-                                           int warp, int lane) {
+template <int EPI, class Src>
+__device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, Bars br, volatile int* abort_flag,
+                                           int SL, int warp, int lane) {
   const int q = warp & 3;                  // TMEM lane quarter this warp may access
   const int half = (warp - 2) >> 2;        // which 128 of the tile's 256 columns
   const int row_in_tile = q * 32 + lane;
   const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
   int buf = 0;
   uint32_t buf_phase = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t bi, bj;
-    tile_coords(t, tm, tn, tri, bi, bj);
+  for (int64_t t = blockIdx.x; t < src.ntiles; t += gridDim.x) {
+    TileCtx ctx;
+    if (!src.get(t, ctx)) continue;
+    const TcArgs& p = *ctx.args;
+    const int64_t nslices = (ctx.nk + SL - 1) / SL;
     float acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
@@ -416,12 +498,13 @@ __device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, 
       if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
     }
     if (!ok) return;
-    const int64_t r = bi * BM + row_in_tile;
+    const bool tri = p.triangular != 0;
+    const int64_t r = ctx.bi * BM + row_in_tile;
     const bool row_ok = r < p.M;
     double part = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int64_t c0 = bj * BN + half * 128 + c * 32;
+      const int64_t c0 = ctx.bj * BN + half * 128 + c * 32;
       float* v = &acc[c * 32];
       if (!row_ok || c0 >= p.N) continue;
       const bool full_chunk = c0 + 32 <= p.N;
@@ -456,12 +539,14 @@ __device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, 
           }
         }
       } else if (EPI == TC_EPI_GRAM) {
+        // planes of G for entries on and above the diagonal, mirrored below it
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
+        uint16_t* pt = p.out_planes + c0 * p.ldo + r;
         float s_off = 0.f, s_diag = 0.f;
         if (full_chunk && r < c0) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
-          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+          store_planes32_mirror(pr, pt, p.ldo, p.out_plane_stride, p.out_nplanes, v);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -472,6 +557,7 @@ __device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, 
                 s_diag = fmaf(d, d, s_diag);
               } else {
                 s_off = fmaf(v[j], v[j], s_off);
+                store_planes1(pt + j * p.ldo, p.out_plane_stride, p.out_nplanes, v[j]);
               }
               store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
             }
@@ -493,19 +579,16 @@ __device__ __noinline__ void role_epilogue(const TcArgs& p, uint32_t tmem_base, 
     if (EPI == TC_EPI_GRAM) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-      if (lane == 0) p.partials[t * EPI_WARPS + (warp - 2)] = part;
+      if (lane == 0) p.partials[ctx.part + (warp - 2)] = part;
     }
   }
 }
 
-template <int P, bool A_MN, bool B_MN, int EPI>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ TcArgs p, int64_t tm, int64_t tn, int64_t ntiles) {
+// Shared prologue/epilogue of both launch forms; `Src` supplies the tiles.
+template <int P, bool A_MN, bool B_MN, int EPI, class Src>
+__device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, int SL, const int* planes_dyn) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
-  if (p.st && p.st->status != ST_RUNNING) return;
-
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::STAGE_BYTES);
@@ -544,28 +627,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const bool tri = p.triangular != 0;
-  const int64_t nk = (p.K + BK - 1) / BK;
-  const int SL = p.slice_stages > 0 ? p.slice_stages : 1;   // k-stages per promoted slice
-  const int64_t nslices = (nk + SL - 1) / SL;
 
   if (warp == 0) {
-    if (lane == 0) role_producer<P, A_MN, B_MN>(&tmA, &tmB, smem_base, br, abort_flag, tm, tn, ntiles, nk, tri);
+    if (lane == 0) role_producer<P, A_MN, B_MN>(src, smem_base, br, abort_flag);
   } else if (warp == 1) {
     if (lane == 0) {
-      const int pu = p.planes_dyn ? min(max(*p.planes_dyn, 1), P) : P;
-      role_mma<P, A_MN, B_MN>(smem_base, tmem_base, br, abort_flag, ntiles, nk, SL, pu);
+      const int pu = planes_dyn ? min(max(*planes_dyn, 1), P) : P;
+      role_mma<P, A_MN, B_MN>(src, smem_base, tmem_base, br, abort_flag, SL, pu);
     }
   } else {
-    role_epilogue<EPI>(p, tmem_base, br, abort_flag, tm, tn, ntiles, nslices, tri, warp, lane);
+    role_epilogue<EPI>(src, tmem_base, br, abort_flag, SL, warp, lane);
   }
 
   tc_fence_before();
   __syncthreads();
+  if (*abort_flag && threadIdx.x == 0 && err_word) atomicOr(err_word, 1);
   if (*abort_flag && threadIdx.x == 0) {
-    if (p.st) {
-      atomicOr(&p.st->err_flags, 1u);
-      p.st->status = ST_TIMEOUT;  // later launches of this solve return at once
+    if (st) {
+      atomicOr(&st->err_flags, 1u);
+      st->status = ST_TIMEOUT;  // later launches of this solve return at once
     } else {
       atomicOr(&g_tc_error, 1u);
     }
@@ -575,6 +655,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                  : "memory");
   }
+}
+
+template <int P, bool A_MN, bool B_MN, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ TcArgs p, int64_t tm, int64_t tn, int64_t ntiles) {
+  if (p.st && p.st->status != ST_RUNNING) return;
+  SingleSrc src;
+  src.ma = &tmA;
+  src.mb = &tmB;
+  src.args = &p;
+  src.tm = tm;
+  src.tn = tn;
+  src.ntiles = ntiles;
+  src.nk = (p.K + BK - 1) / BK;
+  src.tri = p.triangular != 0;
+  tc_body<P, A_MN, B_MN, EPI>(src, p.st, nullptr, p.slice_stages > 0 ? p.slice_stages : 1, p.planes_dyn);
+}
+
+template <int P, bool A_MN, bool B_MN, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_grouped_kernel(const __grid_constant__ TcGroupLaunch g) {
+  if (g.done && *g.done) return;
+  GroupSrc src;
+  src.tiles = g.tiles;
+  src.entries = g.entries;
+  src.ntiles = g.ntiles;
+  tc_body<P, A_MN, B_MN, EPI>(src, nullptr, g.err, g.slice_stages > 0 ? g.slice_stages : 1, g.planes_dyn);
 }
 
 // ---------------------------------------------------------------- host side
@@ -715,6 +822,51 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
     case 1: return dispatch_p<1>(ma, mb, a, tm, tn, ntiles, s);
     case 2: return dispatch_p<2>(ma, mb, a, tm, tn, ntiles, s);
     default: return dispatch_p<3>(ma, mb, a, tm, tn, ntiles, s);
+  }
+}
+
+}  // namespace polar
+
+// ---------------------------------------------------------------- grouped launches
+
+namespace polar {
+namespace {
+
+template <int P, bool A_MN, bool B_MN, int EPI>
+cudaError_t launch_grouped_t(const TcGroupLaunch& g, cudaStream_t s) {
+  auto k = tc_gemm_grouped_kernel<P, A_MN, B_MN, EPI>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P>::SMEM);
+  if (e != cudaSuccess) return e;
+  int64_t grid = g.ntiles < sm_count() ? g.ntiles : sm_count();
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, NTHREADS, Cfg<P>::SMEM, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t dispatch_grouped(const TcGroupLaunch& g, cudaStream_t s) {
+  if (g.epi == TC_EPI_NS && !g.a_mn && g.b_mn) return launch_grouped_t<P, false, true, TC_EPI_NS>(g, s);
+  if (g.epi == TC_EPI_GRAM && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_GRAM>(g, s);
+  if (g.epi == TC_EPI_STORE && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_STORE>(g, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool tc_make_entry_maps(TcGroupEntry* e) {
+  const TcArgs& a = e->args;
+  return make_map(reinterpret_cast<CUtensorMap*>(e->map_a), a.a, a.nplanes, !a.a.kmajor, BM) &&
+         make_map(reinterpret_cast<CUtensorMap*>(e->map_b), a.b, a.nplanes, !a.b.kmajor, BN);
+}
+
+cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g_in, cudaStream_t s) {
+  TcGroupLaunch g = g_in;
+  if (g.nplanes < 1 || g.nplanes > 3 || !g.tiles || !g.entries) return cudaErrorInvalidValue;
+  if (g.slice_stages <= 0) g.slice_stages = default_slice_stages(g.nplanes);
+  switch (g.nplanes) {
+    case 1: return dispatch_grouped<1>(g, s);
+    case 2: return dispatch_grouped<2>(g, s);
+    default: return dispatch_grouped<3>(g, s);
   }
 }
 

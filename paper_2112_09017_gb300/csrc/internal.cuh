@@ -121,7 +121,43 @@ struct TcArgs {
                                                   // planes (schedules); outputs keep out_nplanes
 };
 cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s);
+
+// Grouped launch: many independent problems in one persistent launch. Each problem
+// has an entry (its TMA maps and its own TcArgs: sizes, epilogue pointers, status);
+// the tile table lists (problem, tile row, tile column, tile index within the problem)
+// in the order CTAs take them. Tiles of problems whose status is not RUNNING are skipped.
+struct TcGroupEntry {
+  alignas(128) unsigned char map_a[128];  // CUtensorMap
+  alignas(128) unsigned char map_b[128];
+  TcArgs args;                            // per problem: M, N, K, epilogue fields, st
+};
+struct TcTile {
+  int32_t prob, bi, bj, local;
+};
+struct TcGroupLaunch {
+  int nplanes, epi, a_mn, b_mn;           // shared by every problem of the launch
+  const TcTile* tiles;                    // device
+  int64_t ntiles;
+  const TcGroupEntry* entries;            // device
+  const int* done;                        // device flag: nonzero -> the launch returns at once
+  int* err;                               // device word: set to 1 when a bounded wait expired
+  const int* planes_dyn;
+  int slice_stages;
+};
+cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g, cudaStream_t s);
+// Fills entry->map_a / map_b for the operands of entry->args (host side).
+bool tc_make_entry_maps(TcGroupEntry* entry);
 int tc_gram_partials(int64_t n);
 bool tc_available();
+
+// ---------------------------------------------------------------------------------
+// Batched solves (batched.cu)
+struct BatchedPlan;
+polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, const int64_t* n,
+                              const polar_options_t& opt, int prec);
+polar_status_t batched_run(BatchedPlan* bp, const float* const* A, float* const* U, float* const* H, double tol,
+                           int32_t* iters_dev, double* resid_dev, cudaStream_t s);
+void batched_destroy(BatchedPlan* bp);
+size_t batched_workspace_bytes(const BatchedPlan* bp);
 
 }  // namespace polar

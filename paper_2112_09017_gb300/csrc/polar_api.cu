@@ -118,6 +118,7 @@ struct polar_plan_s {
   size_t prof_used = 0;
   // batched
   int count = 0;
+  BatchedPlan* bp = nullptr;
   std::vector<polar_plan_t> subplans;
 };
 
@@ -213,6 +214,10 @@ void plan_free(polar_plan_s* p) {
     delete sp;
   }
   p->subplans.clear();
+  if (p->bp) {
+    batched_destroy(p->bp);
+    p->bp = nullptr;
+  }
 }
 
 polar_status_t plan_setup(polar_plan_s* p) {
@@ -365,11 +370,10 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
   e = launch_tc_gemm(g, s);
   if (e != cudaSuccess) return e;
   if ((e = prof_end(p, pi, s)) != cudaSuccess) return e;
-  p->launches += 3;
+  p->launches += 2;
   // the finalize records the planes this Gram used (schedules: read on the device)
-  e = launch_residual_finalize(p->partials, tc_gram_partials(p->n), p->st, rule, k, rule.sched ? -1 : p->P, s);
-  if (e != cudaSuccess) return e;
-  return launch_mirror_planes(p->Gp, p->ldp, p->gps, kStoredPlanes, p->n, p->st, nullptr, s);
+  // (the Gram epilogue stores the mirrored lower triangle itself)
+  return launch_residual_finalize(p->partials, tc_gram_partials(p->n), p->st, rule, k, rule.sched ? -1 : p->P, s);
 }
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
@@ -553,7 +557,7 @@ polar_status_t polar_plan_create(polar_plan_t* plan, int64_t m, int64_t n, const
 
 size_t polar_plan_workspace_bytes(polar_plan_t plan) {
   if (!plan) return 0;
-  size_t b = plan->ws_bytes;
+  size_t b = plan->ws_bytes + batched_workspace_bytes(plan->bp);
   for (auto sp : plan->subplans) b += sp->ws_bytes;
   return b;
 }
@@ -585,14 +589,39 @@ polar_status_t polar_batched_plan_create(polar_plan_t* plan, int count, const in
   if (count < 1 || !m || !n) return POLAR_EINVAL;
   for (int i = 0; i < count; ++i)
     if (n[i] < 1 || m[i] < n[i]) return POLAR_EINVAL;
-  return POLAR_ENOTSUP;
+  polar_options_t opt;
+  if (o) opt = *o; else polar_default_options(&opt);
+  normalize_options(opt);
+  int prec = opt.prec == POLAR_AUTO ? POLAR_BF16X6 : opt.prec;
+  if (prec < 0 || prec > POLAR_BF16) return POLAR_EINVAL;
+  // batched problems run on the tensor-core path with a fixed plane count
+  if (prec != POLAR_BF16X6 && prec != POLAR_BF16X3 && prec != POLAR_BF16) return POLAR_ENOTSUP;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  if (!tc_available()) return POLAR_ENOTSUP;
+  polar_plan_s* p = new (std::nothrow) polar_plan_s();
+  if (!p) return POLAR_ENOMEM;
+  p->batched = true;
+  p->count = count;
+  p->opt = opt;
+  p->prec = prec;
+  polar_status_t r = batched_create(&p->bp, count, m, n, opt, prec);
+  if (r != POLAR_OK) {
+    delete p;
+    cudaGetLastError();
+    return r;
+  }
+  *plan = p;
+  return POLAR_OK;
 }
 
 polar_status_t polar_batched_run(polar_plan_t plan, const float* const* A, float* const* U, float* const* H,
                                  double tol, int32_t* iters_dev, double* resid_dev, polar_stream_t stream) {
-  (void)tol; (void)iters_dev; (void)resid_dev; (void)stream;
-  if (!plan || !plan->batched || !A || !U || !H) return POLAR_EINVAL;
-  return POLAR_ENOTSUP;
+  if (!plan || !plan->batched || !plan->bp || !A || !U || !H) return POLAR_EINVAL;
+  for (int i = 0; i < plan->count; ++i)
+    if (!A[i] || !U[i] || !H[i]) return POLAR_EINVAL;
+  polar_status_t r = batched_run(plan->bp, A, U, H, tol, iters_dev, resid_dev, (cudaStream_t)stream);
+  if (r == POLAR_ECUDA) cudaGetLastError();
+  return r;
 }
 
 polar_status_t polar_split_bf16(const float* X, int64_t count, int planes, uint16_t* out, polar_stream_t stream) {
