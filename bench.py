@@ -7,6 +7,7 @@ matrix with a prescribed spectrum, input resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload square8192_k1e4] [--prec bf16x6] [--no-plain] [--no-cpu]
+                  [--batched 4096]
 
 Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
 problem of the same size (independent replicas; the single solve does not shard),
@@ -35,6 +36,32 @@ def algorithmic_flops(m, n, iters):
     """(iters + 1) Grams of m n^2 (symmetric half), iters updates of 2 m n^2, and
     U^T A for H (2 m n^2): m n^2 (3 iters + 3)."""
     return float(m) * n * n * (3 * iters + 3)
+
+
+def kernel_source_hash():
+    """First 16 hex digits of sha256 over the tensor-core kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("gemm_tc.cu", "internal.cuh", "device_util.cuh"):
+        with open(os.path.join(ROOT, "paper_2112_09017_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per update launch from the committed ncu summary of this workload,
+    or None when there is none or the kernel source changed since it was captured."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"tc_gemm_update_{workload.split('_')[0]}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"Kernel source hash[^:]*:\s*([0-9a-f]{16})", text)
+    m_traf = re.search(r"traffic per launch \(read \+ write\) \| ([0-9.e+]+) B", text)
+    if not m_hash or not m_traf or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_traf.group(1))
 
 
 def load_peaks():
@@ -120,14 +147,21 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world, work_per_rank, ms_max):
+    """Whole-job throughput: every rank's work over the slowest rank's time (weak scaling:
+    each rank solves its own problem of the same size)."""
+    return world * work_per_rank / (ms_max * 1e-3)
 
 
 def accuracy(torch, A, U, H, q1q2t=None):
@@ -164,6 +198,53 @@ def cpu_cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+def run_batched(lib, torch, count, steps, warmup):
+    """The batched workload: `count` problems (n uniform on [64, 1024], m = n or 2n,
+    sigma on [1e-3, 1]) in one polar_batched_run; solves/s and per-problem iterations."""
+    from paper_2112_09017_gb300 import synth
+    t0 = time.perf_counter()
+    As = [synth.batched_problem_on_device(i, "cuda") for i in range(count)]
+    gen_s = time.perf_counter() - t0
+    ms = [a.shape[0] for a in As]
+    ns = [a.shape[1] for a in As]
+    Us = [torch.empty_like(a) for a in As]
+    Hs = [torch.empty((n, n), dtype=torch.float32, device="cuda") for n in ns]
+    o = lib.polar_default_options()
+    o.prec = lib.POLAR_BF16X6
+    t0 = time.perf_counter()
+    plan = lib.polar_batched_plan_create(ms, ns, o)
+    plan_s = time.perf_counter() - t0
+    it = torch.zeros(count, dtype=torch.int32, device="cuda")
+    rs = torch.zeros(count, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lib.polar_batched_run(plan, As, Us, Hs, 0.0, it, rs)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        lib.polar_batched_run(plan, As, Us, Hs, 0.0, it, rs)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_run = ev0.elapsed_time(ev1) / steps
+    iters = it.cpu().numpy()
+    conv = iters >= 0
+    k = [int(x) if x >= 0 else -1 - int(x) for x in iters]
+    flops = sum(float(m) * n * n * (3 * kk + 3) for m, n, kk in zip(ms, ns, k))
+    acc = []
+    for i in (0, count // 2, count - 1):
+        acc.append(accuracy(torch, As[i], Us[i], Hs[i]))
+    lib.polar_plan_destroy(plan)
+    import numpy as np
+    return {"workload": f"batched{count}_k1e3", "count": count, "ms_per_batch": ms_run,
+            "solves_per_s": count / (ms_run * 1e-3), "value": flops / (ms_run * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "converged": int(conv.sum()), "iters_p50": float(np.percentile(k, 50)),
+            "iters_p99": float(np.percentile(k, 99)), "max_residual": float(rs.max().item()),
+            "orth_bwd_sampled": [(a["orth"], a["bwd"]) for a in acc], "launch": "one CUDA graph per batch",
+            "inputs": "drawn on the device (same size law and recipe, torch generator, float32 QR)",
+            "generate_s": gen_s, "plan_s": plan_s}
 
 
 def run_reference(args):
@@ -240,8 +321,8 @@ def run_ours(args):
     ms, infos, clocks = timed(plan, args.steps, args.warmup, sampler)
     iters = infos[-1]["iters"]
     flops = sum(algorithmic_flops(m, n, i["iters"]) for i in infos)
-    value = world * flops / (ms * 1e-3) / 1e12
-    solves_per_s = world * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, flops, ms) / 1e12
+    solves_per_s = whole_job_rate(world, args.steps, ms)
     acc = accuracy(torch, A, U, H, torch.from_numpy(q1 @ q2.T).cuda() if rank == 0 else None)
 
     # dominant kernel: the update product X <- 1.5 X - 0.5 X G (2/3 of the flops)
@@ -258,7 +339,8 @@ def run_ours(args):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             ach = work / avg_s / 1e12
             roofline = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                        "frac": ach / peak, "traffic": None, "kernel": "update product (tcgen05, split BF16)",
+                        "frac": ach / peak, "traffic": profiled_traffic(w.name),
+                        "kernel": "update product (tcgen05, split BF16)",
                         "peak_source": f"{peak_src} bf16 sustained", "launch_ms": avg_s * 1e3}
         else:
             work = 2.0 * m * n * n
@@ -308,6 +390,11 @@ def run_ours(args):
                  "ms_per_step": pms / len(pinfos), "iters": pinfos[-1]["iters"], **pacc}
         pplan.close()
 
+    # ---- batched configuration beside the single solve ----
+    batched = None
+    if args.batched > 0:
+        batched = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if not args.no_cpu and world == 1:
@@ -335,6 +422,7 @@ def run_ours(args):
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -353,6 +441,7 @@ def main():
     ap.add_argument("--prec", default="bf16x6")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched", type=int, default=4096, help="problems in the batched leg (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -357,9 +357,11 @@ struct GroupSrc {
 };
 
 template <int P, bool A_MN, bool B_MN, class Src>
-__device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, Bars br, volatile int* abort_flag) {
+__device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, Bars br, volatile int* abort_flag,
+                                           int withhold) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
+  if (withhold) return;  // test hook: no copies are issued, the consumers' bounded waits expire
   int stage = 0;
   uint32_t phase = 0;
   uint32_t armed = 0, armed_phase = 0;  // bit s: stage s was armed / the parity it was armed with
@@ -586,7 +588,8 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
 
 // Shared prologue/epilogue of both launch forms; `Src` supplies the tiles.
 template <int P, bool A_MN, bool B_MN, int EPI, class Src>
-__device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, int SL, const int* planes_dyn) {
+__device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, int SL, const int* planes_dyn,
+                                        int withhold) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -629,7 +632,7 @@ __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_w
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) role_producer<P, A_MN, B_MN>(src, smem_base, br, abort_flag);
+    if (lane == 0) role_producer<P, A_MN, B_MN>(src, smem_base, br, abort_flag, withhold);
   } else if (warp == 1) {
     if (lane == 0) {
       const int pu = planes_dyn ? min(max(*planes_dyn, 1), P) : P;
@@ -671,7 +674,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   src.ntiles = ntiles;
   src.nk = (p.K + BK - 1) / BK;
   src.tri = p.triangular != 0;
-  tc_body<P, A_MN, B_MN, EPI>(src, p.st, nullptr, p.slice_stages > 0 ? p.slice_stages : 1, p.planes_dyn);
+  tc_body<P, A_MN, B_MN, EPI>(src, p.st, nullptr, p.slice_stages > 0 ? p.slice_stages : 1, p.planes_dyn,
+                              p.withhold_tma);
 }
 
 template <int P, bool A_MN, bool B_MN, int EPI>
@@ -681,7 +685,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_grouped_kernel(const __gr
   src.tiles = g.tiles;
   src.entries = g.entries;
   src.ntiles = g.ntiles;
-  tc_body<P, A_MN, B_MN, EPI>(src, nullptr, g.err, g.slice_stages > 0 ? g.slice_stages : 1, g.planes_dyn);
+  tc_body<P, A_MN, B_MN, EPI>(src, nullptr, g.err, g.slice_stages > 0 ? g.slice_stages : 1, g.planes_dyn,
+                              g.withhold_tma);
 }
 
 // ---------------------------------------------------------------- host side
@@ -797,9 +802,18 @@ int default_slice_stages(int planes) {
   return planes == 3 ? 2 : planes == 2 ? 4 : 8;
 }
 
+// Test hook for the bounded waits: with POLAR_TEST_WITHHOLD_TMA=1 in the environment
+// the producer issues no copies, so the consumers' waits expire after about one
+// second and the launch reports a timeout instead of computing.
+int withhold_tma() {
+  const char* e = getenv("POLAR_TEST_WITHHOLD_TMA");
+  return (e && e[0] == '1') ? 1 : 0;
+}
+
 cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
   TcArgs a = a_in;
   if (a.slice_stages <= 0) a.slice_stages = default_slice_stages(a.nplanes);
+  a.withhold_tma = withhold_tma();
   if (a.nplanes < 1 || a.nplanes > 3 || a.M <= 0 || a.N <= 0 || a.K <= 0) return cudaErrorInvalidValue;
   const TcOperand* ops[2] = {&a.a, &a.b};
   for (const TcOperand* o : ops)
@@ -863,6 +877,7 @@ cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g_in, cudaStream_t s) {
   TcGroupLaunch g = g_in;
   if (g.nplanes < 1 || g.nplanes > 3 || !g.tiles || !g.entries) return cudaErrorInvalidValue;
   if (g.slice_stages <= 0) g.slice_stages = default_slice_stages(g.nplanes);
+  g.withhold_tma = withhold_tma();
   switch (g.nplanes) {
     case 1: return dispatch_grouped<1>(g, s);
     case 2: return dispatch_grouped<2>(g, s);

@@ -119,6 +119,8 @@ struct TcArgs {
   int slice_stages;                               // k-stages per promoted slice (0: library default)
   const int* planes_dyn;                          // if non-null: passes use min(*planes_dyn, nplanes)
                                                   // planes (schedules); outputs keep out_nplanes
+  int withhold_tma;                               // test hook: the producer issues no copies, so the
+                                                  // bounded waits expire (set by the launcher)
 };
 cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s);
 
@@ -143,6 +145,7 @@ struct TcGroupLaunch {
   int* err;                               // device word: set to 1 when a bounded wait expired
   const int* planes_dyn;
   int slice_stages;
+  int withhold_tma;                       // test hook, as in TcArgs
 };
 cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g, cudaStream_t s);
 // Fills entry->map_a / map_b for the operands of entry->args (host side).

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "haar_columns", "logspace_spectrum", "two_segment_spectrum", "matrix_with_spectrum",
-    "Workload", "WORKLOADS", "make_workload", "batched_sizes", "batched_problem",
+    "Workload", "WORKLOADS", "make_workload", "batched_sizes", "batched_problem", "batched_problem_on_device",
 ]
 
 
@@ -140,3 +140,30 @@ def batched_problem(i: int, sigma_min: float = 1e-3, n_lo: int = 64, n_hi: int =
     if return_factors:
         return a32, (q1, sigma, q2)
     return a32
+
+
+def batched_problem_on_device(i: int, device, sigma_min: float = 1e-3, n_lo: int = 64, n_hi: int = 1024):
+    """Problem i of the batched workload drawn on a CUDA device, for benchmark inputs
+    where generating thousands of QR factors on the host is too slow.
+
+    Same size law as ``batched_problem`` (sizes from default_rng(i)) and the same
+    recipe (Haar Q1, Q2 from QR of Gaussians, sign-fixed; log-spaced sigma), but the
+    Gaussians come from torch's generator seeded with i and the QR runs in float32
+    on the device, so the values differ from ``batched_problem``'s.
+    """
+    import torch
+    rng = np.random.default_rng(i)
+    n = int(rng.integers(n_lo, n_hi + 1))
+    m = n if rng.random() < 0.5 else 2 * n
+    g = torch.Generator(device=device).manual_seed(i)
+
+    def haar(rows, cols):
+        q, r = torch.linalg.qr(torch.randn(rows, cols, device=device, generator=g))
+        d = torch.sign(torch.diagonal(r))
+        d[d == 0] = 1.0
+        return q * d[None, :]
+
+    q1 = haar(m, n)
+    q2 = haar(n, n)
+    sigma = torch.from_numpy(logspace_spectrum(n, sigma_min)).to(device=device, dtype=torch.float32)
+    return ((q1 * sigma[None, :]) @ q2.T).contiguous()

@@ -1,0 +1,84 @@
+"""The multi-rank host logic of bench.py on CPU: world size 2 over gloo on 127.0.0.1.
+The single solve does not shard (independent replicas), so the only cross-rank
+steps are the barrier and the max over ranks of the timed region."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    bench.barrier(world)
+    ms = bench.max_over_ranks(100.0 + 50.0 * rank, world, device="cpu")
+    rate = bench.whole_job_rate(world, 3.0e12, ms)
+    bench.barrier(world)
+    dist.destroy_process_group()
+    q.put((rank, ms, rate))
+
+
+def test_two_rank_timing_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    # both ranks see the slowest rank's time; the rate counts both ranks' work
+    assert [g[1] for g in got] == [150.0, 150.0]
+    assert got[0][2] == pytest.approx(2 * 3.0e12 / 0.150)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        workload = "square512_k1e2"
+        steps = 1
+        warmup = 0
+    assert bench.run_reference(A()) == 0
+    assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """--impl reference on rank 0: the oracle on bounded samples, one JSON line."""
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        workload = "square512_k1e2"
+        steps = 2
+        warmup = 1
+    assert bench.run_reference(A()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "TFLOP/s" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["config"]["workload"] == "square512_k1e2"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
