@@ -31,8 +31,10 @@
 //                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
 //                        also stored at its mirror position) and float64
 //                        partials of ||G - I||_F^2 per tile and warp
-// Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-slices)
-// or MN-major (stored K x MN, 128-byte swizzle, 64-element MN chunks).
+// Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-stages)
+// or MN-major (stored K x MN, 128-byte swizzle, 64-element MN chunks); three
+// 72 KiB stages for three planes. (16-element stages, six of 36 KiB, keep more
+// bytes in flight but measured slower: twice the per-stage barrier work.)
 // Every mbarrier wait is bounded (about one second); on expiry the kernel
 // records an error flag, lets its copies and MMAs drain, frees TMEM and returns.
 #include <cuda.h>
@@ -51,17 +53,22 @@ __device__ unsigned int g_tc_error;  // timeouts of launches without a plan stat
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int BM = 128, BN = 256, BK = 32;   // two K=16 MMA steps per k-stage
 constexpr int NTHREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr uint32_t A_PLANE = BM * BK * 2;  // 8 KiB per plane per stage
 constexpr uint32_t B_PLANE = BN * BK * 2;  // 16 KiB
+// MN-major operands: 64-column chunks of BK rows x 128 bytes (128-byte swizzle)
+constexpr uint32_t MN_CHUNK = 64 * BK * 2;
+// K-major operands: rows of BK elements (BK * 2 bytes), swizzle of that width, 8-row groups
+constexpr uint32_t KM_SBO = 8 * BK * 2;
+constexpr uint32_t KM_SWZ = BK == 16 ? 6 : BK == 32 ? 4 : 2;   // descriptor codes: 32, 64, 128-byte swizzle
 constexpr uint32_t TMEM_COLS = 512;        // two 128 x 256 FP32 slice accumulators
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
 template <int P>
 struct Cfg {
-  static constexpr int STAGES = P == 3 ? 3 : (P == 2 ? 4 : 8);
+  static constexpr int STAGES = (P == 3 ? 6 : (P == 2 ? 9 : 16)) * 16 / BK;
   static constexpr uint32_t A_BYTES = P * A_PLANE;
   static constexpr uint32_t B_BYTES = P * B_PLANE;
   static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
@@ -243,6 +250,21 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t tm, int64_t tn, b
 
 // ---------------------------------------------------------------- epilogue pieces
 
+// Three BF16 planes of two values at once: each plane is the round-to-nearest-even
+// BF16 of what the previous planes left (cvt.rn.bf16x2.f32 packs b into the low
+// half and a into the high half, so element 0 lands at the lower address).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t (&w)[3]) {
+  float r0 = x0, r1 = x1;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    uint32_t h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(r1), "f"(r0));
+    w[q] = h;
+    r0 = r0 - __uint_as_float(h << 16);
+    r1 = r1 - __uint_as_float(h & 0xffff0000u);
+  }
+}
+
 __device__ __forceinline__ void store_planes32(uint16_t* base, int64_t pstride, int np, const float* x) {
   // x: 32 consecutive values; writes np planes, 64 bytes each, 16-byte aligned
 #pragma unroll
@@ -250,11 +272,10 @@ __device__ __forceinline__ void store_planes32(uint16_t* base, int64_t pstride, 
     uint32_t w[3][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uint16_t a[3], b[3];
-      split_planes_dev<3>(x[8 * v + 2 * i], a);
-      split_planes_dev<3>(x[8 * v + 2 * i + 1], b);
+      uint32_t t[3];
+      split2(x[8 * v + 2 * i], x[8 * v + 2 * i + 1], t);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) w[q][i] = (uint32_t)a[q] | ((uint32_t)b[q] << 16);
+      for (int q = 0; q < 3; ++q) w[q][i] = t[q];
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -271,15 +292,14 @@ __device__ __forceinline__ void store_planes32_mirror(uint16_t* base, uint16_t* 
     uint32_t w[3][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      uint16_t a[3], b[3];
-      split_planes_dev<3>(x[8 * v + 2 * i], a);
-      split_planes_dev<3>(x[8 * v + 2 * i + 1], b);
+      uint32_t t[3];
+      split2(x[8 * v + 2 * i], x[8 * v + 2 * i + 1], t);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        w[q][i] = (uint32_t)a[q] | ((uint32_t)b[q] << 16);
+        w[q][i] = t[q];
         if (q < np) {
-          tbase[q * pstride + (int64_t)(8 * v + 2 * i) * ld] = a[q];
-          tbase[q * pstride + (int64_t)(8 * v + 2 * i + 1) * ld] = b[q];
+          tbase[q * pstride + (int64_t)(8 * v + 2 * i) * ld] = (uint16_t)(t[q] & 0xffffu);
+          tbase[q * pstride + (int64_t)(8 * v + 2 * i + 1) * ld] = (uint16_t)(t[q] >> 16);
         }
       }
     }
@@ -290,9 +310,9 @@ __device__ __forceinline__ void store_planes32_mirror(uint16_t* base, uint16_t* 
 }
 
 __device__ __forceinline__ void store_planes1(uint16_t* base, int64_t pstride, int np, float x) {
-  uint16_t a[3];
-  split_planes_dev<3>(x, a);
-  for (int q = 0; q < np; ++q) base[q * pstride] = a[q];
+  uint32_t t[3];
+  split2(x, 0.0f, t);
+  for (int q = 0; q < np; ++q) base[q * pstride] = (uint16_t)(t[q] & 0xffffu);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -387,13 +407,13 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
       const int k0 = (int)(kb * BK);
       if (A_MN) {
 #pragma unroll
-        for (int cc = 0; cc < BM / 64; ++cc) tma_load_3d(a_dst + cc * P * 4096, c.ma, fb, m0 + 64 * cc, k0, 0);
+        for (int cc = 0; cc < BM / 64; ++cc) tma_load_3d(a_dst + cc * P * MN_CHUNK, c.ma, fb, m0 + 64 * cc, k0, 0);
       } else {
         tma_load_3d(a_dst, c.ma, fb, k0, m0, 0);
       }
       if (B_MN) {
 #pragma unroll
-        for (int cc = 0; cc < BN / 64; ++cc) tma_load_3d(b_dst + cc * P * 4096, c.mb, fb, n0 + 64 * cc, k0, 0);
+        for (int cc = 0; cc < BN / 64; ++cc) tma_load_3d(b_dst + cc * P * MN_CHUNK, c.mb, fb, n0 + 64 * cc, k0, 0);
       } else {
         tma_load_3d(b_dst, c.mb, fb, k0, n0, 0);
       }
@@ -414,8 +434,8 @@ __device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, ui
   for (int ps = 0; ps < passes_for(NP); ++ps) {
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
-      const uint32_t aoff = A_MN ? pass_a(NP, ps) * 4096 + kk * 2048 : pass_a(NP, ps) * A_PLANE + kk * 32;
-      const uint32_t boff = B_MN ? pass_b(NP, ps) * 4096 + kk * 2048 : pass_b(NP, ps) * B_PLANE + kk * 32;
+      const uint32_t aoff = A_MN ? pass_a(NP, ps) * MN_CHUNK + kk * 2048 : pass_a(NP, ps) * A_PLANE + kk * 32;
+      const uint32_t boff = B_MN ? pass_b(NP, ps) * MN_CHUNK + kk * 2048 : pass_b(NP, ps) * B_PLANE + kk * 32;
       tc_mma(d_tmem, a_desc + (aoff >> 4), b_desc + (boff >> 4), idesc, (ps == 0 && kk == 0) ? first_acc : 1u);
     }
   }
@@ -426,9 +446,10 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
                                       volatile int* abort_flag, int SL, int pu) {
   using C = Cfg<P>;
   constexpr int S = C::STAGES;
-  const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * 4096, 1024, 2) : smem_desc(smem_base, 16, 512, 4);
-  const uint64_t b_desc0 = B_MN ? smem_desc(smem_base + C::A_BYTES, P * 4096, 1024, 2)
-                                : smem_desc(smem_base + C::A_BYTES, 16, 512, 4);
+  const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * MN_CHUNK, 1024, 2)
+                                : smem_desc(smem_base, 16, KM_SBO, KM_SWZ);
+  const uint64_t b_desc0 = B_MN ? smem_desc(smem_base + C::A_BYTES, P * MN_CHUNK, 1024, 2)
+                                : smem_desc(smem_base + C::A_BYTES, 16, KM_SBO, KM_SWZ);
   int stage = 0;
   uint32_t phase = 0;
   int buf = 0;
@@ -498,6 +519,19 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       __syncwarp();
       if (lane == 0) mbar_arrive(br.tempty0 + 8 * buf);
       if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+      if (EPI == TC_EPI_NS && sl == (nslices > 1 ? nslices - 2 : 0)) {
+        // the output step reads this row's 128 columns of X_k's three planes: pull them into L2 now
+        const int64_t r = ctx.bi * BM + row_in_tile;
+        const int64_t c0 = ctx.bj * BN + half * 128;
+        if (r < p.M && c0 < p.N) {
+          const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + q * p.x_plane_stride + 64 * l));
+        }
+      }
     }
     if (!ok) return;
     const bool tri = p.triangular != 0;
@@ -725,7 +759,7 @@ bool make_map(CUtensorMap* map, const TcOperand& op, int nplanes, bool mn_major,
     swz = CU_TENSOR_MAP_SWIZZLE_128B;
   } else {
     box[0] = BK; box[1] = (cuuint32_t)mn_box; box[2] = (cuuint32_t)nplanes;
-    swz = CU_TENSOR_MAP_SWIZZLE_64B;
+    swz = BK == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : BK == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   }
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(op.planes), dims, strides, box,
                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -787,11 +821,10 @@ int tc_gram_partials(int64_t n) {
   return (int)(tri_tiles(tm, tn) * EPI_WARPS);
 }
 
-// k-stages per promoted slice. Each slice accumulates 2 x passes MMAs per stage
-// with round-toward-zero before its round-to-nearest promotion; 24 MMAs per slice
-// for 3 and 2 planes (64 and 128 of K) and 16 for one plane (256 of K) keep the
-// promotion work below the MMA time of a slice. POLAR_TC_SLICE_STAGES (1..16)
-// overrides it for tuning.
+// k-stages per promoted slice. Each slice accumulates passes x K/16 MMAs with
+// round-toward-zero before its round-to-nearest promotion; 64 of K for three
+// planes (24 MMAs), 128 for two and 256 for one keep the promotion work below the
+// MMA time of a slice. POLAR_TC_SLICE_STAGES (1..16) overrides it for tuning.
 int default_slice_stages(int planes) {
   static int env = [] {
     const char* e = getenv("POLAR_TC_SLICE_STAGES");
@@ -799,7 +832,8 @@ int default_slice_stages(int planes) {
     return (x >= 1 && x <= 16) ? x : 0;
   }();
   if (env) return env;
-  return planes == 3 ? 2 : planes == 2 ? 4 : 8;
+  static_assert(BK == 16 || BK == 32, "slice lengths are multiples of the k-stage width");
+  return (planes == 3 ? 64 : planes == 2 ? 128 : 256) / BK;
 }
 
 // Test hook for the bounded waits: with POLAR_TEST_WITHHOLD_TMA=1 in the environment

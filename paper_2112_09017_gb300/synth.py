@@ -28,6 +28,7 @@ import numpy as np
 __all__ = [
     "haar_columns", "logspace_spectrum", "two_segment_spectrum", "matrix_with_spectrum",
     "Workload", "WORKLOADS", "make_workload", "batched_sizes", "batched_problem", "batched_problem_on_device",
+    "matrix_with_spectrum_on_device",
 ]
 
 
@@ -167,3 +168,28 @@ def batched_problem_on_device(i: int, device, sigma_min: float = 1e-3, n_lo: int
     q2 = haar(n, n)
     sigma = torch.from_numpy(logspace_spectrum(n, sigma_min)).to(device=device, dtype=torch.float32)
     return ((q1 * sigma[None, :]) @ q2.T).contiguous()
+
+
+def matrix_with_spectrum_on_device(m: int, n: int, sigma: np.ndarray, seed: int, device, qr_dtype=None,
+                                   return_factors: bool = False):
+    """A = fl32(Q1 diag(sigma) Q2^T) drawn on a CUDA device (large workloads whose
+    host-side QR takes minutes): same recipe as ``matrix_with_spectrum`` with the
+    Gaussians from torch's generator seeded with `seed` and the QR and product in
+    `qr_dtype` (float64 by default) on the device."""
+    import torch
+    qd = qr_dtype or torch.float64
+    g = torch.Generator(device=device).manual_seed(seed)
+
+    def haar(rows, cols):
+        q, r = torch.linalg.qr(torch.randn(rows, cols, device=device, generator=g, dtype=qd))
+        d = torch.sign(torch.diagonal(r))
+        d[d == 0] = 1.0
+        return q * d[None, :]
+
+    q1 = haar(m, n)
+    q2 = haar(n, n)
+    s = torch.from_numpy(np.asarray(sigma, dtype=np.float64)).to(device=device, dtype=qd)
+    a = ((q1 * s[None, :]) @ q2.T).to(torch.float32).contiguous()
+    if return_factors:
+        return a, (q1, s, q2)
+    return a

@@ -205,3 +205,53 @@ def test_full_size_square8192_bf16x6(lib, torch_cuda):
 
 def test_full_size_square8192_fp32(lib, torch_cuda):
     _full_size(lib, torch_cuda, "fp32")
+
+
+# ------------------------------------------------------------------ the other spectra, scaled down and full size
+
+@pytest.mark.parametrize("shape,spectrum", [((4096, 1024), "k1e6"), ((1024, 1024), "two_segment_k1e8")])
+def test_polar_bf16x6_large_kappa_spectra_match_oracle(lib, torch_cuda, shape, spectrum):
+    """The tall kappa=1e6 and the two-segment kappa=1e8 spectra at oracle-sized shapes."""
+    torch = torch_cuda
+    m, n = shape
+    sigma = synth.logspace_spectrum(n, 1e-6) if spectrum == "k1e6" else synth.two_segment_spectrum(n)
+    kappa = 1e6 if spectrum == "k1e6" else 1e8
+    a, (q1, s, q2) = synth.matrix_with_spectrum(m, n, sigma, 0, return_factors=True)
+    ref = ns_polar(a, tol=1e-12, count_tol=1e-6)
+    plan = lib.Plan(m, n, prec="bf16x6", tol=1e-6)
+    U, H, info = plan(torch.from_numpy(a).cuda())
+    plan.close()
+    assert info["status"] == lib.POLAR_OK
+    assert abs(info["iters"] - ref["iters_at"]) <= 1
+    assert ref["iters_at"] == scalar.predict_ns(sigma, 1e-6)["iters"]
+    met = metrics(a, to_np(U), to_np(H), ref["U"])
+    assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, met
+    assert met["fwd"] <= 1e-7 * kappa, met
+
+
+def test_full_size_tall32768x8192(lib, torch_cuda):
+    """The tall workload at full size (drawn on the device with float64 QR): the
+    iteration count of its spectrum, sampled orth and bwd in float64, fwd against
+    the closed form within 1e-7 kappa."""
+    torch = torch_cuda
+    w = synth.WORKLOADS["tall32768x8192_k1e6"]
+    A, (q1, s, q2) = synth.matrix_with_spectrum_on_device(w.m, w.n, w.spectrum(), w.seed, "cuda", torch.float64,
+                                                          return_factors=True)
+    uex = (q1 @ q2.T).float()
+    del q1, q2
+    plan = lib.Plan(w.m, w.n, prec="bf16x6", tol=w.tol)
+    U, H, info = plan(A)
+    plan.close()
+    want = json.load(open(os.path.join(GOLDEN, "iteration_counts.json")))["workloads"][w.name]["iters"]
+    assert info["status"] == lib.POLAR_OK and abs(info["iters"] - want) <= 1
+    n, k = w.n, 512
+    S = torch.randperm(n, generator=torch.Generator(device="cuda").manual_seed(0), device="cuda")[:k]
+    U64 = U.double()
+    rows = U64[:, S].T @ U64
+    rows[torch.arange(k, device="cuda"), S] -= 1.0
+    orth = math.sqrt(rows.square().sum().item() / k)
+    R = A[:, S].double() - U64 @ H[:, S].double()
+    bwd = math.sqrt(R.square().sum().item() / k * n) / torch.linalg.matrix_norm(A.double()).item()
+    fwd = (torch.linalg.matrix_norm((U - uex).double()) / math.sqrt(n)).item()
+    assert orth <= 5e-6 and bwd <= 5e-6, (orth, bwd)
+    assert fwd <= 1e-7 * w.kappa, fwd
