@@ -36,8 +36,10 @@ import math
 
 import numpy as np
 
-__all__ = ["frobenius_norm", "gram_residual", "ns_polar", "orth_error",
-           "backward_error", "symmetry_error", "forward_error"]
+__all__ = ["frobenius_norm", "gram_residual", "ns_polar", "ns_polar_preconditioned", "precond_step_count",
+           "orth_error", "backward_error", "symmetry_error", "forward_error"]
+
+EPS32 = 2.0 ** -23  # single-precision machine epsilon, the default s0 of Algorithm 1
 
 
 def frobenius_norm(a: np.ndarray) -> float:
@@ -103,6 +105,71 @@ def ns_polar(a, tol: float = 1e-12, max_iter: int = 100, stagnation: float = 0.7
     h = 0.5 * (c + c.T)                                 # H = sym(U^T A)
     return {"U": u, "H": h, "iters": k, "residuals": residuals, "status": status,
             "normA": s, "iters_at": iters_at}
+
+
+def precond_step_count(s_minus: float, s0: float | None = None, max_steps: int = 1000) -> int:
+    """Steps of the first loop of Algorithm 1: feed s0 (machine epsilon when not
+    supplied) through Eq. RogueScalar until it reaches s_minus."""
+    a = 1.5 * math.sqrt(3.0) - s_minus                  # Eq. a_def
+    s = EPS32 if s0 is None or s0 <= 0 else s0
+    k = 0
+    while s < s_minus and k < max_steps:
+        s = a * s * (1.0 - (4.0 / 27.0) * a * a * s * s)  # Eq. RogueScalar
+        k += 1
+    return k
+
+
+def ns_polar_preconditioned(a, s_minus: float = 0.1, s0: float | None = None, tol: float = 1e-12,
+                            max_iter: int = 100, stagnation: float = 0.7, stag_floor: float = 1e-4,
+                            count_tol: float | None = None) -> dict:
+    """Algorithm 1 (preconditioned Newton-Schulz) in float64.
+
+    U <- A / ||A||_F; p = the number of Eq. RogueScalar steps that lift s0 to
+    s_minus; then p steps of Eq. RogueMatrix, X <- a X (I - 4/27 a^2 X^T X) with
+    a = 3 sqrt(3)/2 - s_minus (Eq. a_def), followed by the Newton-Schulz steps of
+    Eq. NewtonSchulz with the residual stop rule of ``ns_polar`` (tested only once
+    the preconditioning steps are done). Every step forms the Gram G = X^T X and
+    records r = ||G - I||_F / sqrt(n). Returns the dict of ``ns_polar`` plus
+    "n_precond".
+    """
+    a_mat = np.asarray(a, dtype=np.float64)
+    m, n = a_mat.shape
+    if m < n or n < 1:
+        raise ValueError("A must be m x n with m >= n >= 1")
+    p = precond_step_count(s_minus, s0)
+    coef = 1.5 * math.sqrt(3.0) - s_minus
+    s = frobenius_norm(a_mat)
+    if not math.isfinite(s) or s == 0.0:
+        return {"U": None, "H": None, "iters": 0, "residuals": [], "status": "nonfinite", "normA": s,
+                "iters_at": None, "n_precond": p}
+    x = a_mat / s
+    residuals: list[float] = []
+    iters_at = None
+    status = "not_converged"
+    k = 0
+    while True:
+        g = x.T @ x
+        r = gram_residual(g)
+        residuals.append(r)
+        if k >= p:
+            if count_tol is not None and iters_at is None and r <= count_tol:
+                iters_at = k
+            if r <= tol:
+                status = "converged"
+                break
+            if k >= p + 2 and r > stagnation * residuals[k - 2] and r < stag_floor:
+                break
+        if k >= max_iter:
+            break
+        if k < p:
+            x = coef * x - (4.0 / 27.0) * coef ** 3 * (x @ g)   # Eq. RogueMatrix
+        else:
+            x = 1.5 * x - 0.5 * (x @ g)                          # Eq. NewtonSchulz
+        k += 1
+    c = x.T @ a_mat
+    h = 0.5 * (c + c.T)
+    return {"U": x, "H": h, "iters": k, "residuals": residuals, "status": status, "normA": s,
+            "iters_at": iters_at, "n_precond": p}
 
 
 def orth_error(u: np.ndarray) -> float:

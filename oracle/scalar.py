@@ -22,8 +22,8 @@ import math
 
 import numpy as np
 
-__all__ = ["ns_step", "precond_a", "precond_step", "predict_ns", "precond_steps_needed",
-           "ns_steps_to_one"]
+__all__ = ["ns_step", "precond_a", "precond_step", "predict_ns", "predict_preconditioned",
+           "precond_steps_needed", "ns_steps_to_one"]
 
 
 def ns_step(x):
@@ -80,3 +80,19 @@ def ns_steps_to_one(x0: float, eps: float, max_steps: int = 1000) -> int:
         x = ns_step(x)
         k += 1
     return k
+
+
+def predict_preconditioned(sigma, tol: float, n_precond: int, s_minus: float, max_iter: int = 200) -> dict:
+    """Exact-arithmetic residual trajectory of Algorithm 1 on a matrix with singular
+    values ``sigma``: x_0 = sigma / ||sigma||_2, n_precond steps of Eq. RogueScalar,
+    then Eq. NS_scalar; "iters" is the first k >= n_precond with r_k <= tol."""
+    s = np.asarray(sigma, dtype=np.float64)
+    x = s / math.sqrt(float(np.sum(s * s)))
+    res = []
+    for k in range(max_iter + 1):
+        r = math.sqrt(float(np.mean((x * x - 1.0) ** 2)))
+        res.append(r)
+        if k >= n_precond and r <= tol:
+            return {"iters": k, "residuals": res}
+        x = precond_step(x, s_minus) if k < n_precond else ns_step(x)
+    return {"iters": None, "residuals": res}
