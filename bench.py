@@ -7,7 +7,7 @@ matrix with a prescribed spectrum, input resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload square8192_k1e4] [--prec bf16x6] [--no-plain] [--no-cpu]
-                  [--batched 4096]
+                  [--batched 4096] [--no-precond]
 
 Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
 problem of the same size (independent replicas; the single solve does not shard),
@@ -390,6 +390,18 @@ def run_ours(args):
                  "ms_per_step": pms / len(pinfos), "iters": pinfos[-1]["iters"], **pacc}
         pplan.close()
 
+    # ---- Algorithm 1 (preconditioned iteration) on the same input, beside the fixed form ----
+    pre = None
+    if not args.no_precond:
+        qplan = lib.Plan(m, n, prec=args.prec, tol=w.tol, precondition=1)
+        qms, qinfos, _ = timed(qplan, max(1, min(args.steps, 3)), min(args.warmup, 3))
+        qacc = accuracy(torch, A, U, H)
+        qplan.close()
+        qsteps = len(qinfos)
+        pre = {"ms_per_step": qms / qsteps, "solves_per_s": whole_job_rate(world, qsteps, qms),
+               "iters": qinfos[-1]["iters"], "n_precond": qinfos[-1]["n_precond"], **qacc,
+               "speedup_vs_fixed_form": (ms / args.steps) / (qms / qsteps)}
+
     # ---- batched configuration beside the single solve ----
     batched = None
     if args.batched > 0:
@@ -422,7 +434,7 @@ def run_ours(args):
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-            "batched": batched,
+            "batched": batched, "preconditioned": pre,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -442,6 +454,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=4096, help="problems in the batched leg (0: skip)")
+    ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned (Algorithm 1) leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -80,6 +80,11 @@ typedef struct {
   double switch_residual;  /* schedules: residual below which the finer precision is used; <= 0 means 1e-2 */
   size_t ws_limit;         /* maximum workspace bytes a plan may allocate; 0 = no limit */
   int profile;             /* nonzero: time every Gram and update launch with CUDA events (info) */
+  int precondition;        /* nonzero: Algorithm 1 - first the steps X <- a X (I - 4/27 a^2 X^T X),
+                              a = 3 sqrt(3)/2 - s_minus (Eqs. a_def, RogueMatrix), as many as lift s0 to
+                              s_minus under Eq. RogueScalar; then Newton-Schulz. Stop tests start after them */
+  double s_minus;          /* preconditioning threshold; <= 0 means 0.1 */
+  double s0;               /* estimate of the smallest singular value of A / ||A||_F; <= 0 means 2^-23 */
 } polar_options_t;
 
 #define POLAR_HIST 128
@@ -95,6 +100,7 @@ typedef struct {
   float ms_total;             /* device time of the whole solve (CUDA events), milliseconds */
   int launches;               /* kernels this run enqueued (including ones that found the run stopped) */
   int n_gram, n_update;       /* profile: Gram and update launches that did work */
+  int n_precond;              /* preconditioning steps among the iters updates (0 without preconditioning) */
   float ms_gram, ms_update;   /* profile: their summed device time (CUDA events), milliseconds */
   double res_hist[POLAR_HIST];         /* r_k for k = 0 .. hist_len-1 */
   unsigned char planes_hist[POLAR_HIST];/* BF16 planes of the Gram at step k (0 = FP32 SIMT) */

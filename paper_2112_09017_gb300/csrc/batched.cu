@@ -88,6 +88,8 @@ __global__ void b_norm_kernel(const float* const* __restrict__ A, const BMeta* _
     s.err_flags = 0;
     s.planes_next = planes_first;
     s.sym_err = 0.0;
+    s.upd_c1 = 1.5f;
+    s.upd_c3 = -0.5f;
     for (int i = 0; i < 4; ++i) s.ring[i] = 0.0;
     s.status = (isfinite(nrm) && nrm > 0.0) ? ST_RUNNING : ST_NONFINITE;
     if (p == 0) {
@@ -143,12 +145,16 @@ __global__ void b_finalize_kernel(const BMeta* __restrict__ meta, DevState* __re
   s.ring[k & 3] = r;
   s.iters = k;
   const double tol = sh->tol > 0 ? sh->tol : rule.tol;
+  const bool testing = k >= rule.n_pre;  // Algorithm 1: no stop test during preconditioning
   if (!isfinite(r)) s.status = ST_NONFINITE;
-  else if (r <= tol) s.status = ST_CONVERGED;
-  else if (k >= 2 && r > rule.stagnation * r2 && r < rule.stag_floor) s.status = ST_NOT_CONVERGED;
+  else if (testing && r <= tol) s.status = ST_CONVERGED;
+  else if (testing && k >= rule.n_pre + 2 && r > rule.stagnation * r2 && r < rule.stag_floor)
+    s.status = ST_NOT_CONVERGED;
   else if (k >= rule.max_iter) s.status = ST_NOT_CONVERGED;
   else {
     s.planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
+    s.upd_c1 = k < rule.n_pre ? (float)rule.pre_a : 1.5f;
+    s.upd_c3 = k < rule.n_pre ? (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a) : -0.5f;
     atomicAdd(&sh->running[k < POLAR_HIST + 8 ? k : POLAR_HIST + 7], 1);
   }
 }
@@ -324,6 +330,8 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   rule.max_iter = b->opt.max_iter;
   rule.sched = b->prec == POLAR_SCHED_BF16_THEN_X3 ? 1 : 0;
   rule.planes_fixed = b->P;
+  rule.n_pre = b->opt.precondition ? precond_steps(b->opt.s_minus, b->opt.s0) : 0;
+  rule.pre_a = 1.5 * sqrt(3.0) - b->opt.s_minus;
   const int planes_first = rule.sched ? 1 : b->P;
 #define BK_(x) do { if ((x) != cudaSuccess) return POLAR_ECUDA; } while (0)
   b_norm_kernel<<<count, kThreads, 0, s>>>(b->A_tab, b->meta_d, b->st_d, b->sh_d, planes_first);

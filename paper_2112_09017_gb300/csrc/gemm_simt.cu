@@ -197,17 +197,18 @@ __global__ void __launch_bounds__(NT) simt_gemm_kernel(SimtArgs p, bool vec_a, b
             if (c0 + j < p.N) dst[j] = p.alpha * v[j] + (p.beta != 0.0f ? p.beta * dst[j] : 0.0f);
         }
       } else if (EPI == SIMT_EPI_NS) {
+        // X_{k+1} = c1 X_k + c3 X_k G (1.5, -0.5; or Algorithm 1's preconditioning coefficients)
+        const float c1 = p.st ? p.st->upd_c1 : 1.5f, c3 = p.st ? p.st->upd_c3 : -0.5f;
         const float* xo = p.Xold + r * p.ldx + c0;
         float* dst = p.C + r * p.ldc + c0;
         if (vec_c && c0 + 3 < p.N) {
           float4 x = *reinterpret_cast<const float4*>(xo);
           *reinterpret_cast<float4*>(dst) =
-              make_float4(1.5f * x.x - 0.5f * v[0], 1.5f * x.y - 0.5f * v[1], 1.5f * x.z - 0.5f * v[2],
-                          1.5f * x.w - 0.5f * v[3]);
+              make_float4(c1 * x.x + c3 * v[0], c1 * x.y + c3 * v[1], c1 * x.z + c3 * v[2], c1 * x.w + c3 * v[3]);
         } else {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (c0 + j < p.N) dst[j] = 1.5f * xo[j] - 0.5f * v[j];
+            if (c0 + j < p.N) dst[j] = c1 * xo[j] + c3 * v[j];
         }
       } else {  // GRAM: store the tile; residual weights 2 above the diagonal, 1 on it
         float* dst = p.C + r * p.ldc + c0;

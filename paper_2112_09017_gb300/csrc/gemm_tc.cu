@@ -26,7 +26,8 @@
 //               tcgen05.ld of every slice, running sums in registers, then the
 //               fused output step of the tile:
 //                 STORE  C = alpha acc + beta C   (optionally upper triangle)
-//                 NS     X_{k+1} = 1.5 X_k - 0.5 acc, X_k read from its three
+//                 NS     X_{k+1} = c1 X_k + c3 acc (1.5, -0.5, or the preconditioning
+//                        coefficients of Algorithm 1), X_k read from its three
 //                        BF16 planes (an exact FP32 encoding), written as planes
 //                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
 //                        also stored at its mirror position) and float64
@@ -535,6 +536,9 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     }
     if (!ok) return;
     const bool tri = p.triangular != 0;
+    // update coefficients of this step (1.5, -0.5 for Newton-Schulz; a, -4/27 a^3 while preconditioning)
+    const float c1 = (EPI == TC_EPI_NS && p.st) ? p.st->upd_c1 : 1.5f;
+    const float c3 = (EPI == TC_EPI_NS && p.st) ? p.st->upd_c3 : -0.5f;
     const int64_t r = ctx.bi * BM + row_in_tile;
     const bool row_ok = r < p.M;
     double part = 0.0;
@@ -545,7 +549,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       if (!row_ok || c0 >= p.N) continue;
       const bool full_chunk = c0 + 32 <= p.N;
       if (EPI == TC_EPI_NS) {
-        // X_{k+1} = 1.5 X_k - 0.5 X_k G: X_k from its three planes (exact), result as planes
+        // X_{k+1} = c1 X_k + c3 X_k G: X_k from its three planes (exact), result as planes
         const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
         if (full_chunk) {
@@ -560,7 +564,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
               const int w = e >> 1, sh = (e & 1) * 16;
               const float x = (bf16_to_f32_dev((uint16_t)(hw[w] >> sh)) + bf16_to_f32_dev((uint16_t)(mw[w] >> sh))) +
                               bf16_to_f32_dev((uint16_t)(lw[w] >> sh));
-              v[8 * i + e] = 1.5f * x - 0.5f * v[8 * i + e];
+              v[8 * i + e] = c1 * x + c3 * v[8 * i + e];
             }
           }
           store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
@@ -570,7 +574,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
             if (c0 + j < p.N) {
               const float x = (bf16_to_f32_dev(xr[j]) + bf16_to_f32_dev(xr[p.x_plane_stride + j])) +
                               bf16_to_f32_dev(xr[2 * p.x_plane_stride + j]);
-              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, 1.5f * x - 0.5f * v[j]);
+              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, c1 * x + c3 * v[j]);
             }
           }
         }

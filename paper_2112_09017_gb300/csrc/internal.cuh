@@ -27,6 +27,7 @@ struct DevState {
   int hist_len;
   unsigned int err_flags;// device error bits (timeouts)
   int pad;
+  float upd_c1, upd_c3;  // the next update is X <- upd_c1 X + upd_c3 X G
   double ring[4];        // r_k at slot k % 4 (stagnation test beyond the history)
   double sym_err;        // ||skew(U^T A)||_F / ||U^T A||_F
   double res_hist[POLAR_HIST];
@@ -42,7 +43,11 @@ struct StopRule {
   int max_iter;
   int sched;      // 0: fixed planes, 1: BF16 then BF16X3
   int planes_fixed;
+  int n_pre;      // preconditioning steps (Algorithm 1) before the Newton-Schulz steps
+  double pre_a;   // their coefficient a = 3 sqrt(3)/2 - s_minus
 };
+// Number of Eq. RogueScalar steps lifting s0 to s_minus (the first loop of Algorithm 1).
+int precond_steps(double s_minus, double s0);
 
 // ---------------------------------------------------------------------------------
 // Misc kernels (kernels_misc.cu)

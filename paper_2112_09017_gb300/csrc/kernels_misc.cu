@@ -68,6 +68,8 @@ __global__ void norm_finalize_kernel(const double* __restrict__ partials, int np
     st->err_flags = 0;
     st->planes_next = planes_first;
     st->sym_err = 0.0;
+    st->upd_c1 = 1.5f;
+    st->upd_c3 = -0.5f;
     for (int i = 0; i < 4; ++i) st->ring[i] = 0.0;
     st->status = (isfinite(nrm) && nrm > 0.0) ? ST_RUNNING : ST_NONFINITE;
   }
@@ -125,16 +127,24 @@ __global__ void residual_finalize_kernel(const double* __restrict__ partials, in
   double r2 = (k >= 2) ? st->ring[(k - 2) & 3] : 0.0;
   st->ring[k & 3] = r;
   st->iters = k;
+  const bool testing = k >= rule.n_pre;  // Algorithm 1: no stop test during preconditioning
   if (!isfinite(r)) {
     st->status = ST_NONFINITE;
-  } else if (r <= rule.tol) {
+  } else if (testing && r <= rule.tol) {
     st->status = ST_CONVERGED;
-  } else if (k >= 2 && r > rule.stagnation * r2 && r < rule.stag_floor) {
+  } else if (testing && k >= rule.n_pre + 2 && r > rule.stagnation * r2 && r < rule.stag_floor) {
     st->status = ST_NOT_CONVERGED;
   } else if (k >= rule.max_iter) {
     st->status = ST_NOT_CONVERGED;
   } else {
     st->planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
+    if (k < rule.n_pre) {  // Eq. RogueMatrix: X <- a X - (4/27) a^3 X G
+      st->upd_c1 = (float)rule.pre_a;
+      st->upd_c3 = (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a);
+    } else {               // Eq. NewtonSchulz: X <- 1.5 X - 0.5 X G
+      st->upd_c1 = 1.5f;
+      st->upd_c3 = -0.5f;
+    }
   }
 }
 
@@ -242,6 +252,18 @@ __global__ void copy2d_kernel(const float* __restrict__ src, int64_t lds, float*
 int grid_rows(int64_t m) { return (int)(m < 4096 ? (m > 0 ? m : 1) : 4096); }
 
 }  // namespace
+
+int precond_steps(double s_minus, double s0) {
+  // Algorithm 1, first loop: s <- a s (1 - 4/27 a^2 s^2) until s >= s_minus (Eqs. a_def, RogueScalar)
+  const double a = 1.5 * sqrt(3.0) - s_minus;
+  double s = s0;
+  int k = 0;
+  while (s < s_minus && k < 1000) {
+    s = a * s * (1.0 - (4.0 / 27.0) * a * a * s * s);
+    ++k;
+  }
+  return k;
+}
 
 int frob_partials_blocks(int64_t m, int64_t n) {
   (void)n;

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -134,6 +135,10 @@ void polar_default_options(polar_options_t* o) {
   o->stag_floor = 1e-4;
   o->switch_residual = 1e-2;
   o->ws_limit = 0;
+  o->profile = 0;
+  o->precondition = 0;
+  o->s_minus = 0.1;
+  o->s0 = 0.0;
 }
 
 const char* polar_status_string(polar_status_t s) {
@@ -176,6 +181,8 @@ void normalize_options(polar_options_t& o) {
   if (!(o.stagnation > 0)) o.stagnation = 0.7;
   if (!(o.stag_floor > 0)) o.stag_floor = 1e-4;
   if (!(o.switch_residual > 0)) o.switch_residual = 1e-2;
+  if (!(o.s_minus > 0) || o.s_minus >= 1.0) o.s_minus = 0.1;
+  if (!(o.s0 > 0)) o.s0 = 1.1920928955078125e-07;  // 2^-23, single-precision machine epsilon
 }
 
 int resolve_prec(int prec, int64_t n) {
@@ -279,6 +286,8 @@ StopRule make_rule(const polar_plan_s* p, double tol) {
   r.max_iter = p->opt.max_iter;
   r.sched = p->prec == POLAR_SCHED_BF16_THEN_X3 ? 1 : 0;
   r.planes_fixed = p->P;
+  r.n_pre = p->opt.precondition ? precond_steps(p->opt.s_minus, p->opt.s0) : 0;
+  r.pre_a = 1.5 * sqrt(3.0) - p->opt.s_minus;
   return r;
 }
 
@@ -510,6 +519,7 @@ polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U
     info->sym_err = h.sym_err;
     info->ms_total = ms;
     info->launches = p->launches;
+    info->n_precond = std::min(rule.n_pre, it);
     for (size_t i = 0; i < p->prof_used; ++i) {
       const auto& pr = p->prof[i];
       if ((pr.kind == 0 && pr.k > it) || (pr.kind == 1 && pr.k >= it)) continue;  // launches after the stop

@@ -27,14 +27,16 @@ PASSES = {0: 0, 1: 1, 2: 3, 3: 6}
 
 class polar_options_t(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int), ("stagnation", C.c_double),
-                ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int)]
+                ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int),
+                ("precondition", C.c_int), ("s_minus", C.c_double), ("s0", C.c_double)]
 
 
 class polar_info_t(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("prec", C.c_int), ("hist_len", C.c_int),
                 ("residual", C.c_double), ("normA_F", C.c_double), ("sym_err", C.c_double),
                 ("ms_total", C.c_float), ("launches", C.c_int), ("n_gram", C.c_int), ("n_update", C.c_int),
-                ("ms_gram", C.c_float), ("ms_update", C.c_float), ("res_hist", C.c_double * POLAR_HIST),
+                ("n_precond", C.c_int), ("ms_gram", C.c_float), ("ms_update", C.c_float),
+                ("res_hist", C.c_double * POLAR_HIST),
                 ("planes_hist", C.c_ubyte * POLAR_HIST)]
 
     def as_dict(self):
@@ -42,6 +44,7 @@ class polar_info_t(C.Structure):
         return {"status": self.status, "iters": self.iters, "prec": self.prec, "residual": self.residual,
                 "normA_F": self.normA_F, "sym_err": self.sym_err, "ms_total": self.ms_total,
                 "launches": self.launches, "n_gram": self.n_gram, "n_update": self.n_update,
+                "n_precond": self.n_precond,
                 "ms_gram": self.ms_gram, "ms_update": self.ms_update,
                 "res_hist": list(self.res_hist[:n]), "planes_hist": list(self.planes_hist[:n])}
 

@@ -22,12 +22,13 @@ def torch_cuda():
     return torch
 
 
-def _run_batch(lib, torch, mats, prec="bf16x6", tol=1e-6, reps=1):
+def _run_batch(lib, torch, mats, prec="bf16x6", tol=1e-6, reps=1, precondition=0):
     ms = [a.shape[0] for a in mats]
     ns = [a.shape[1] for a in mats]
     o = lib.polar_default_options()
     o.prec = lib.PREC[prec]
     o.tol = tol
+    o.precondition = precondition
     plan = lib.polar_batched_plan_create(ms, ns, o)
     As = [torch.from_numpy(a).cuda() for a in mats]
     outs = []
@@ -107,3 +108,17 @@ def test_batched_rejects_bad_arguments(lib, torch_cuda):
     with pytest.raises(lib.PolarError) as e:
         lib.polar_batched_plan_create([8], [8], o)
     assert e.value.code == lib.POLAR_ENOTSUP
+
+
+def test_batched_preconditioned_matches_oracle(lib, torch_cuda):
+    from oracle.ns_polar import ns_polar_preconditioned
+    torch = torch_cuda
+    sizes = [(64, 64), (257, 129), (300, 300), (520, 260)]
+    mats = [synth.matrix_with_spectrum(m, n, synth.logspace_spectrum(n, 1e-4), 200 + i)
+            for i, (m, n) in enumerate(sizes)]
+    (Us, Hs, iters, res), = _run_batch(lib, torch, mats, precondition=1)
+    for i, a in enumerate(mats):
+        ref = ns_polar_preconditioned(a, tol=1e-12, count_tol=1e-6)
+        assert abs(iters[i] - ref["iters_at"]) <= 1, (i, iters[i], ref["iters_at"])
+        met = metrics(a, to_np(Us[i]), to_np(Hs[i]), ref["U"])
+        assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, (i, met)
