@@ -390,6 +390,33 @@ def run_ours(args):
                  "ms_per_step": pms / len(pinfos), "iters": pinfos[-1]["iters"], **pacc}
         pplan.close()
 
+    # ---- context: one Newton-Schulz step with cuBLAS FP32 products (TF32 off), per step ----
+    cublas = None
+    if not args.no_plain:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        X = (A / torch.linalg.matrix_norm(A)).contiguous()
+
+        def step():
+            G = X.T @ X
+            return 1.5 * X - 0.5 * (X @ G)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        st_ms = e0.elapsed_time(e1) / 3
+        cublas = {"ms_per_ns_step": st_ms, "est_ms_per_solve": st_ms * (iters + 1),
+                  "note": "torch.matmul FP32 with TF32 off: full X^T X and X G per step (4 m n^2 flops), "
+                          "scaled by the solve's step count; context for the plain-FP32 comparison"}
+        del X
+
     # ---- Algorithm 1 (preconditioned iteration) on the same input, beside the fixed form ----
     pre = None
     if not args.no_precond:
@@ -431,7 +458,7 @@ def run_ours(args):
             "accuracy": acc,
             "kernel_ms": {"gram_avg": ms_gram / max(n_gram, 1), "update_avg": ms_upd / max(n_upd, 1),
                           "n_gram": n_gram, "n_update": n_upd},
-            "plain_fp32": plain,
+            "plain_fp32": plain, "plain_fp32_cublas_context": cublas,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "batched": batched, "preconditioned": pre,

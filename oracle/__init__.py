@@ -11,5 +11,7 @@ Modules:
               the exact-arithmetic residual trajectory predicted from a spectrum
   jacobi_svd  one-sided Jacobi SVD, the independent checker on small inputs
   precision   bit-level BF16 plane split and an emulator of split products
+  ns_inverse  the Newton-Schulz matrix inverse of Algorithm 2 and its trajectory
+              predicted from a spectrum
 """
-from . import jacobi_svd, ns_polar, precision, scalar  # noqa: F401
+from . import jacobi_svd, ns_inverse, ns_polar, precision, scalar  # noqa: F401
