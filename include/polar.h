@@ -170,6 +170,21 @@ POLAR_API polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const flo
 POLAR_API polar_status_t polar_split_bf16(const float* X, int64_t count, int planes, uint16_t* out,
                                 polar_stream_t stream);
 
+/* Newton-Schulz matrix inverse (Algorithm 2) of A (rows x cols, rows >= cols, full column rank,
+ * lda >= cols) into X (cols x rows, ldx >= rows): X_0 = A^T / ||A A^T||_F, then
+ * X <- X (2I - A X) (the X A = I branch; X tends to the pseudo-inverse, A^{-1} when square) until
+ * ||X' - X||_F / ||X'||_F <= u 2^k after update k (u = 2^-24: the paper's doubling tolerance), or
+ * max_iter (<= 0 means 100) updates. The doubling tolerance ends the loop within ~25 updates, so for
+ * ill-conditioned A (kappa >~ 1e2) the result is an approximate inverse. prec: BF16X6, BF16X3 or BF16
+ * (products on the tensor cores with the same promotion as polar_run); FP32 -> ENOTSUP. Device pointers;
+ * allocates its workspace for the call and returns after the result is in X. *iters (updates applied)
+ * and *delta (the last relative change) may be NULL. Returns OK, NOT_CONVERGED (max_iter reached),
+ * ENONFINITE (A zero or non-finite), EINVAL, ENOMEM, ENOTSUP or ECUDA.
+ * Paper: Sec. III.D, Algorithm 2. */
+POLAR_API polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t cols, int64_t lda, float* X,
+                                          int64_t ldx, int prec, int max_iter, int32_t* iters, double* delta,
+                                          polar_stream_t stream);
+
 /* Size of the static device array behind polar_gemm_noalloc (32 MiB). */
 #define POLAR_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -29,6 +29,7 @@
 //                 NS     X_{k+1} = c1 X_k + c3 acc (1.5, -0.5, or the preconditioning
 //                        coefficients of Algorithm 1), X_k read from its three
 //                        BF16 planes (an exact FP32 encoding), written as planes
+//                 PLANES the product itself as BF16 planes (an operand of the next product)
 //                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
 //                        also stored at its mirror position) and float64
 //                        partials of ||G - I||_F^2 per tile and warp
@@ -542,6 +543,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     const int64_t r = ctx.bi * BM + row_in_tile;
     const bool row_ok = r < p.M;
     double part = 0.0;
+    float d2 = 0.f, x2 = 0.f;  // NS with partials: sum (x' - x)^2, sum x'^2 of this thread's row chunk
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int64_t c0 = ctx.bj * BN + half * 128 + c * 32;
@@ -564,7 +566,12 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
               const int w = e >> 1, sh = (e & 1) * 16;
               const float x = (bf16_to_f32_dev((uint16_t)(hw[w] >> sh)) + bf16_to_f32_dev((uint16_t)(mw[w] >> sh))) +
                               bf16_to_f32_dev((uint16_t)(lw[w] >> sh));
-              v[8 * i + e] = c1 * x + c3 * v[8 * i + e];
+              const float xn = c1 * x + c3 * v[8 * i + e];
+              if (p.partials) {
+                d2 = fmaf(xn - x, xn - x, d2);
+                x2 = fmaf(xn, xn, x2);
+              }
+              v[8 * i + e] = xn;
             }
           }
           store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
@@ -574,7 +581,12 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
             if (c0 + j < p.N) {
               const float x = (bf16_to_f32_dev(xr[j]) + bf16_to_f32_dev(xr[p.x_plane_stride + j])) +
                               bf16_to_f32_dev(xr[2 * p.x_plane_stride + j]);
-              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, c1 * x + c3 * v[j]);
+              const float xn = c1 * x + c3 * v[j];
+              if (p.partials) {
+                d2 = fmaf(xn - x, xn - x, d2);
+                x2 = fmaf(xn, xn, x2);
+              }
+              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, xn);
             }
           }
         }
@@ -604,6 +616,16 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
           }
         }
         part += 2.0 * (double)s_off + (double)s_diag;
+      } else if (EPI == TC_EPI_PLANES) {
+        // the product itself as three BF16 planes (an operand of the next product)
+        uint16_t* pr = p.out_planes + r * p.ldo + c0;
+        if (full_chunk) {
+          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < p.N) store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
+        }
       } else {  // STORE
         float* cr = p.C + r * p.ldc + c0;
 #pragma unroll
@@ -620,6 +642,18 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
       if (lane == 0) p.partials[ctx.part + (warp - 2)] = part;
+    }
+    if (EPI == TC_EPI_NS && p.partials) {
+      double a = d2, b = x2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        p.partials[2 * (ctx.part + (warp - 2))] = a;
+        p.partials[2 * (ctx.part + (warp - 2)) + 1] = b;
+      }
     }
   }
 }
@@ -800,6 +834,9 @@ cudaError_t dispatch_p(const CUtensorMap& ma, const CUtensorMap& mb, const TcArg
     case TC_EPI_GRAM:
       if (amn && bmn) return launch_t<P, true, true, TC_EPI_GRAM>(ma, mb, a, tm, tn, ntiles, s);
       return cudaErrorInvalidValue;
+    case TC_EPI_PLANES:
+      if (!amn && bmn) return launch_t<P, false, true, TC_EPI_PLANES>(ma, mb, a, tm, tn, ntiles, s);
+      return cudaErrorInvalidValue;
     default:
       if (amn && bmn) return launch_t<P, true, true, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
       if (!amn && bmn) return launch_t<P, false, true, TC_EPI_STORE>(ma, mb, a, tm, tn, ntiles, s);
@@ -856,7 +893,7 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
   const TcOperand* ops[2] = {&a.a, &a.b};
   for (const TcOperand* o : ops)
     if (!o->planes || !aligned(o->planes, 16) || o->ld % 8 || o->plane_stride % 8) return cudaErrorInvalidValue;
-  if (a.epi == TC_EPI_NS || a.epi == TC_EPI_GRAM) {
+  if (a.epi == TC_EPI_NS || a.epi == TC_EPI_GRAM || a.epi == TC_EPI_PLANES) {
     if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8) return cudaErrorInvalidValue;
     if (a.out_nplanes < 1 || a.out_nplanes > 3) return cudaErrorInvalidValue;
   }

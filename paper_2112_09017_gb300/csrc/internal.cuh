@@ -76,6 +76,13 @@ cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride,
 cudaError_t launch_copy2d(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t m, int64_t n,
                           cudaStream_t s);
 cudaError_t launch_split_flat(const float* x, int64_t count, int nplanes, uint16_t* out, cudaStream_t s);
+// X_0 = A^T / st->normA as three BF16 planes (A rows x cols, X_0 cols x rows).
+cudaError_t launch_transpose_scale_split(const float* A, int64_t lda, int64_t rows, int64_t cols, const DevState* st,
+                                         uint16_t* planes, int64_t ldp, int64_t plane_stride, cudaStream_t s);
+// Newton-Schulz inverse (Algorithm 2): coefficients 2, -1, and the growing-tolerance test after step k.
+cudaError_t launch_inverse_init(DevState* st, cudaStream_t s);
+cudaError_t launch_inverse_finalize(const double* partials, int npairs, DevState* st, int k, int max_iter,
+                                    cudaStream_t s);
 // dst = plane_0 + plane_1 + plane_2 (the FP32 value the three BF16 planes encode exactly)
 cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
                                  float* dst, int64_t ldd, cudaStream_t s);
@@ -100,7 +107,7 @@ int simt_gram_tiles(int64_t n);
 
 // ---------------------------------------------------------------------------------
 // tcgen05 split-BF16 GEMM / SYRK (gemm_tc.cu)
-enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2 };
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2, TC_EPI_PLANES = 3 };
 
 struct TcOperand {
   const uint16_t* planes;  // plane p at planes + p * plane_stride (elements)
@@ -119,7 +126,8 @@ struct TcArgs {
   float* C; int64_t ldc; float alpha, beta;      // STORE
   const uint16_t* x_planes; int64_t ldxp; int64_t x_plane_stride;  // NS: three planes of X_k
   uint16_t* out_planes; int64_t ldo; int64_t out_plane_stride; int out_nplanes; // NS/GRAM plane output
-  double* partials;                               // GRAM residual partials
+  double* partials;                               // GRAM residual partials; NS (if set): per tile and warp
+                                                  // the pair (sum (x' - x)^2, sum x'^2)
   DevState* st;                                   // skip when not RUNNING; error flags
   int slice_stages;                               // k-stages per promoted slice (0: library default)
   const int* planes_dyn;                          // if non-null: passes use min(*planes_dyn, nplanes)

@@ -249,6 +249,67 @@ __global__ void copy2d_kernel(const float* __restrict__ src, int64_t lds, float*
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x) dst[r * ldd + c] = src[r * lds + c];
 }
 
+// X_0[i][j] = A[j][i] / ||A A^T||_F (Algorithm 2) as three BF16 planes, through 32 x 32 shared tiles.
+__global__ void transpose_scale_split_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t cols,
+                                             const DevState* __restrict__ st, uint16_t* __restrict__ P, int64_t ldp,
+                                             int64_t ps) {
+  if (st->status != ST_RUNNING) return;
+  __shared__ float t[32][33];
+  const float sc = (float)st->normA;
+  const int64_t tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t b = blockIdx.x; b < tr * tc; b += gridDim.x) {
+    const int64_t r0 = (b / tc) * 32, c0 = (b % tc) * 32;
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t r = r0 + yy, c = c0 + tx;
+      t[yy][tx] = (r < rows && c < cols) ? A[r * lda + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t i = c0 + yy, j = r0 + tx;  // X_0 row i (a column of A), column j
+      if (i < cols && j < rows) {
+        float rem = __fdiv_rn(t[tx][yy], sc);
+        for (int q = 0; q < 3; ++q) {
+          const uint16_t bq = bf16_rne_bits(rem);
+          P[q * ps + i * ldp + j] = bq;
+          rem = rem - bf16_bits_to_float(bq);
+        }
+      }
+    }
+  }
+}
+
+__global__ void inverse_init_kernel(DevState* st) {
+  st->upd_c1 = 2.0f;   // X' = X (2I - A X) = 2 X - X (A X)
+  st->upd_c3 = -1.0f;
+}
+
+// Algorithm 2's test after update k: delta = ||X' - X||_F / ||X'||_F against eps = u 2^k, u = 2^-24.
+__global__ void inverse_finalize_kernel(const double* __restrict__ partials, int npairs, DevState* st, int k,
+                                        int max_iter) {
+  if (st->status != ST_RUNNING) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  const double sa = block_sum(a);
+  const double sb = block_sum(b);
+  if (threadIdx.x != 0) return;
+  const double delta = sb > 0.0 ? sqrt(sa / sb) : INFINITY;
+  if (k < POLAR_HIST) {
+    st->res_hist[k] = delta;
+    st->hist_len = k + 1;
+  }
+  st->ring[k & 3] = delta;
+  st->iters = k + 1;
+  const double eps = ldexp(1.0, k - 24);
+  if (!isfinite(delta)) st->status = ST_NONFINITE;
+  else if (delta <= eps) st->status = ST_CONVERGED;
+  else if (k + 1 >= max_iter) st->status = ST_NOT_CONVERGED;
+}
+
 int grid_rows(int64_t m) { return (int)(m < 4096 ? (m > 0 ? m : 1) : 4096); }
 
 }  // namespace
@@ -341,6 +402,25 @@ cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride,
 cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
                                  float* dst, int64_t ldd, cudaStream_t s) {
   planes_to_f32_kernel<<<grid_rows(m), kThreads, 0, s>>>(planes, ldp, plane_stride, m, n, dst, ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_scale_split(const float* A, int64_t lda, int64_t rows, int64_t cols, const DevState* st,
+                                         uint16_t* planes, int64_t ldp, int64_t plane_stride, cudaStream_t s) {
+  const int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+  transpose_scale_split_kernel<<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(A, lda, rows, cols, st, planes,
+                                                                                       ldp, plane_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_init(DevState* st, cudaStream_t s) {
+  inverse_init_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_finalize(const double* partials, int npairs, DevState* st, int k, int max_iter,
+                                    cudaStream_t s) {
+  inverse_finalize_kernel<<<1, kThreads, 0, s>>>(partials, npairs, st, k, max_iter);
   return cudaGetLastError();
 }
 

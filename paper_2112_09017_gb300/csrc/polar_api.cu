@@ -739,3 +739,101 @@ polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- Newton-Schulz inverse (Algorithm 2)
+
+extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t cols, int64_t lda, float* X,
+                                           int64_t ldx, int prec, int max_iter, int32_t* iters, double* delta,
+                                           polar_stream_t stream) {
+  if (!A || !X || cols < 1 || rows < cols || lda < cols || ldx < rows) return POLAR_EINVAL;
+  if (overlaps(A, (size_t)((rows - 1) * lda + cols) * 4, X, (size_t)((cols - 1) * ldx + rows) * 4))
+    return POLAR_EINVAL;
+  if (max_iter <= 0) max_iter = 100;
+  if (prec == POLAR_AUTO) prec = POLAR_BF16X6;
+  const int P = planes_of(prec);
+  if (prec == POLAR_SCHED_BF16_THEN_X3 || P == 0) return prec == POLAR_FP32 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  if (!tc_available()) return POLAR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = rows, M = cols;
+  // workspace: A planes (N x M), X planes x2 (M x N, three planes), P = A X planes (N x N, three planes),
+  // C = A^T A (M x M), partials, state
+  const int64_t lpa = round_up(M, 64), lpx = round_up(N, 64);
+  const int64_t sa = round_up(N * lpa, 64), sx = round_up(M * lpx, 64), sp = round_up(N * lpx, 64);
+  const int64_t ldc = round_up(M, 4);
+  const int64_t tiles_ns = ((M + 127) / 128) * ((N + 255) / 256);
+  const int64_t npairs = tiles_ns * 8;
+  const int fb = frob_partials_blocks(M, M);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t o_a = take((size_t)P * sa * 2), o_x0 = take((size_t)3 * sx * 2), o_x1 = take((size_t)3 * sx * 2),
+               o_p = take((size_t)3 * sp * 2), o_c = take((size_t)M * ldc * 4),
+               o_part = take((size_t)std::max<int64_t>(2 * npairs, fb) * 8), o_st = take(sizeof(DevState));
+  void* ws = nullptr;
+  if (cudaMalloc(&ws, off) != cudaSuccess) { cudaGetLastError(); return POLAR_ENOMEM; }
+  uint8_t* w = (uint8_t*)ws;
+  uint16_t* ap = (uint16_t*)(w + o_a);
+  uint16_t* xp[2] = {(uint16_t*)(w + o_x0), (uint16_t*)(w + o_x1)};
+  uint16_t* pp = (uint16_t*)(w + o_p);
+  float* C = (float*)(w + o_c);
+  double* part = (double*)(w + o_part);
+  DevState* st = (DevState*)(w + o_st);
+  polar_status_t ret = POLAR_ECUDA;
+  DevState h;
+  do {
+    if (cudaMemsetAsync(ws, 0, off, s) != cudaSuccess) break;
+    // a = ||A A^T||_F = ||A^T A||_F: the Gram of A's columns on the tensor cores, mirrored, its norm
+    if (launch_scale_split(A, lda, N, M, nullptr, false, nullptr, 0, ap, lpa, sa, P, s) != cudaSuccess) break;
+    TcArgs g{};
+    g.M = M; g.N = M; g.K = N;
+    g.a = op_planes(ap, N, M, lpa, sa, 0);
+    g.b = g.a;
+    g.nplanes = P;
+    g.epi = TC_EPI_STORE; g.triangular = 1;
+    g.C = C; g.ldc = ldc; g.alpha = 1.f; g.beta = 0.f;
+    if (launch_tc_gemm(g, s) != cudaSuccess) break;
+    if (launch_mirror_f32(C, ldc, M, nullptr, s) != cudaSuccess) break;
+    if (launch_frob_partials(C, M, M, ldc, part, fb, s) != cudaSuccess) break;
+    if (launch_norm_finalize(part, fb, st, 1.0, P, s) != cudaSuccess) break;
+    // X_0 = A^T / a; the update X' = 2 X - X (A X)
+    if (launch_transpose_scale_split(A, lda, N, M, st, xp[0], lpx, sx, s) != cudaSuccess) break;
+    if (launch_inverse_init(st, s) != cudaSuccess) break;
+    bool ok = true;
+    for (int k = 0; k < max_iter && ok; ++k) {
+      TcArgs pa{};  // P = A X_k (N x N, K = M)
+      pa.M = N; pa.N = N; pa.K = M;
+      pa.a = op_planes(ap, N, M, lpa, sa, 1);
+      pa.b = op_planes(xp[k & 1], M, N, lpx, sx, 0);
+      pa.nplanes = P;
+      pa.epi = TC_EPI_PLANES;
+      pa.out_planes = pp; pa.ldo = lpx; pa.out_plane_stride = sp; pa.out_nplanes = 3;
+      pa.st = st;
+      TcArgs u{};   // X_{k+1} = 2 X_k - X_k P (M x N, K = N), with the pairs for delta
+      u.M = M; u.N = N; u.K = N;
+      u.a = op_planes(xp[k & 1], M, N, lpx, sx, 1);
+      u.b = op_planes(pp, N, N, lpx, sp, 0);
+      u.nplanes = P;
+      u.epi = TC_EPI_NS;
+      u.x_planes = xp[k & 1]; u.ldxp = lpx; u.x_plane_stride = sx;
+      u.out_planes = xp[(k + 1) & 1]; u.ldo = lpx; u.out_plane_stride = sx; u.out_nplanes = 3;
+      u.partials = part;
+      u.st = st;
+      ok = launch_tc_gemm(pa, s) == cudaSuccess && launch_tc_gemm(u, s) == cudaSuccess &&
+           launch_inverse_finalize(part, (int)npairs, st, k, max_iter, s) == cudaSuccess;
+    }
+    if (!ok) break;
+    if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) break;
+    if (h.err_flags || h.status == ST_TIMEOUT) { ret = POLAR_ETIMEOUT; break; }
+    if (h.status == ST_NONFINITE) { ret = POLAR_ENONFINITE; break; }
+    if (launch_planes_to_f32(xp[h.iters & 1], lpx, sx, M, N, X, ldx, s) != cudaSuccess) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) break;
+    if (iters) *iters = h.iters;
+    if (delta) *delta = h.ring[(h.iters - 1) & 3];
+    ret = h.status == ST_CONVERGED ? POLAR_OK : POLAR_NOT_CONVERGED;
+  } while (0);
+  cudaStreamSynchronize(s);
+  cudaFree(ws);
+  if (ret == POLAR_ECUDA) cudaGetLastError();
+  return ret;
+}

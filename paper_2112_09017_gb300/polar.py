@@ -81,6 +81,7 @@ def load():
         "polar_gemm_noalloc": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
         "polar_syrk": (i32, [i64, i64, f32, vp, i64, f32, vp, i64, i32, vp]),
         "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
+        "polar_ns_inverse": (i32, [vp, i64, i64, i64, vp, i64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
         "polar_device_query": (i32, [C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
@@ -221,6 +222,22 @@ def polar_syrk(A, C_, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None):
                           int(prec), _stream(stream))
     if r != POLAR_OK:
         raise PolarError(r, "polar_syrk")
+
+
+def polar_ns_inverse(A, X, prec=POLAR_BF16X6, max_iter=100, stream=None, raw_status=False):
+    """Newton-Schulz inverse (Algorithm 2) of device tensor A (rows x cols) into X (cols x rows).
+    Returns {"status", "iters", "delta"}."""
+    _check_f32_2d(A, "A"); _check_f32_2d(X, "X")
+    rows, cols = A.shape
+    if tuple(X.shape) != (cols, rows):
+        raise ValueError("X must be cols x rows")
+    it = C.c_int32()
+    d = C.c_double()
+    r = load().polar_ns_inverse(_ptr(A), rows, cols, A.stride(0), _ptr(X), X.stride(0), int(prec), int(max_iter),
+                                C.byref(it), C.byref(d), _stream(stream))
+    if not raw_status and r not in (POLAR_OK, POLAR_NOT_CONVERGED):
+        raise PolarError(r, "polar_ns_inverse")
+    return {"status": r, "iters": it.value, "delta": d.value}
 
 
 def polar_split_bf16(X, planes: int, stream=None):
