@@ -277,6 +277,41 @@ def run_reference(args):
     return 0
 
 
+def run_inverse(lib, torch, m, n, seed, stream, peaks, steps, warmup, world, kappa=10.0):
+    """X A = I by Algorithm 2 for an m x n matrix with a log-spaced spectrum of condition number
+    `kappa`, drawn on the device. Algorithmic work per call: the Gram behind ||A^T A||_F
+    (2 m n^2) and per iteration A X (2 m^2 n) and X (A X) (2 n m^2)."""
+    from paper_2112_09017_gb300 import synth
+    A = synth.matrix_with_spectrum_on_device(m, n, synth.logspace_spectrum(n, 1.0 / kappa), seed, "cuda")
+    X = torch.empty((n, m), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        lib.polar_ns_inverse(A, X, stream=stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = [lib.polar_ns_inverse(A, X, stream=stream) for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    it = outs[-1]["iters"]
+    flops = 2.0 * m * n * n + it * (2.0 * m * m * n + 2.0 * n * m * m)
+    xa = X.double() @ A.double()
+    xa.diagonal().sub_(1.0)
+    resid = float(torch.linalg.matrix_norm(xa)) / n ** 0.5
+    mma = 6.0 * flops / (ms / steps * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained")
+    out = {"value": world * flops * steps / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms / steps,
+           "m": m, "n": n, "kappa": kappa, "iters": it, "delta": outs[-1]["delta"],
+           "status": "converged" if outs[-1]["status"] == lib.POLAR_OK else "not_converged",
+           "xa_minus_i_over_sqrt_n": resid, "bf16_mma_tflops": mma,
+           "tensor_frac_of_measured_sustained": (mma / peak) if peak else None,
+           "note": "whole call (workspace allocation, norm, iterations, output) per step; flops = 2mn^2 + "
+                   "iters x 4m^2n FP32-equivalent; bf16_mma_tflops counts the six split passes"}
+    del A, X, xa
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -429,6 +464,12 @@ def run_ours(args):
                "iters": qinfos[-1]["iters"], "n_precond": qinfos[-1]["n_precond"], **qacc,
                "speedup_vs_fixed_form": (ms / args.steps) / (qms / qsteps)}
 
+    # ---- Algorithm 2 (Newton-Schulz inverse) on a well-conditioned matrix of the same shape ----
+    inverse = None
+    if not args.no_inverse:
+        inverse = run_inverse(lib, torch, m, n, w.seed + 1000 + rank, stream, peaks, max(1, min(args.steps, 3)),
+                              min(args.warmup, 3), world)
+
     # ---- batched configuration beside the single solve ----
     batched = None
     if args.batched > 0:
@@ -461,7 +502,7 @@ def run_ours(args):
             "plain_fp32": plain, "plain_fp32_cublas_context": cublas,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-            "batched": batched, "preconditioned": pre,
+            "batched": batched, "preconditioned": pre, "ns_inverse": inverse,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -482,6 +523,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched", type=int, default=4096, help="problems in the batched leg (0: skip)")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned (Algorithm 1) leg")
+    ap.add_argument("--no-inverse", action="store_true", help="skip the Newton-Schulz inverse (Algorithm 2) leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

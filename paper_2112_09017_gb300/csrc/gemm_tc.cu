@@ -29,6 +29,8 @@
 //                 NS     X_{k+1} = c1 X_k + c3 acc (1.5, -0.5, or the preconditioning
 //                        coefficients of Algorithm 1), X_k read from its three
 //                        BF16 planes (an exact FP32 encoding), written as planes
+//                 NS_STEP NS, plus float64 per-warp sums of (X_{k+1} - X_k)^2 and
+//                        X_{k+1}^2 (the step size of the inverse iteration)
 //                 PLANES the product itself as BF16 planes (an operand of the next product)
 //                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
 //                        also stored at its mirror position) and float64
@@ -504,6 +506,8 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     if (!src.get(t, ctx)) continue;
     const TcArgs& p = *ctx.args;
     const int64_t nslices = (ctx.nk + SL - 1) / SL;
+    constexpr bool NS = EPI == TC_EPI_NS || EPI == TC_EPI_NS_STEP;
+    constexpr bool STEP = EPI == TC_EPI_NS_STEP;
     float acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
@@ -521,7 +525,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       __syncwarp();
       if (lane == 0) mbar_arrive(br.tempty0 + 8 * buf);
       if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
-      if (EPI == TC_EPI_NS && sl == (nslices > 1 ? nslices - 2 : 0)) {
+      if (NS && sl == (nslices > 1 ? nslices - 2 : 0)) {
         // the output step reads this row's 128 columns of X_k's three planes: pull them into L2 now
         const int64_t r = ctx.bi * BM + row_in_tile;
         const int64_t c0 = ctx.bj * BN + half * 128;
@@ -538,19 +542,19 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     if (!ok) return;
     const bool tri = p.triangular != 0;
     // update coefficients of this step (1.5, -0.5 for Newton-Schulz; a, -4/27 a^3 while preconditioning)
-    const float c1 = (EPI == TC_EPI_NS && p.st) ? p.st->upd_c1 : 1.5f;
-    const float c3 = (EPI == TC_EPI_NS && p.st) ? p.st->upd_c3 : -0.5f;
+    const float c1 = (NS && p.st) ? p.st->upd_c1 : 1.5f;
+    const float c3 = (NS && p.st) ? p.st->upd_c3 : -0.5f;
     const int64_t r = ctx.bi * BM + row_in_tile;
     const bool row_ok = r < p.M;
     double part = 0.0;
-    float d2 = 0.f, x2 = 0.f;  // NS with partials: sum (x' - x)^2, sum x'^2 of this thread's row chunk
+    float d2 = 0.f, x2 = 0.f;  // NS_STEP: sum (x' - x)^2 and sum x'^2 over this thread's row chunk
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int64_t c0 = ctx.bj * BN + half * 128 + c * 32;
       float* v = &acc[c * 32];
       if (!row_ok || c0 >= p.N) continue;
       const bool full_chunk = c0 + 32 <= p.N;
-      if (EPI == TC_EPI_NS) {
+      if (NS) {
         // X_{k+1} = c1 X_k + c3 X_k G: X_k from its three planes (exact), result as planes
         const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
@@ -567,7 +571,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
               const float x = (bf16_to_f32_dev((uint16_t)(hw[w] >> sh)) + bf16_to_f32_dev((uint16_t)(mw[w] >> sh))) +
                               bf16_to_f32_dev((uint16_t)(lw[w] >> sh));
               const float xn = c1 * x + c3 * v[8 * i + e];
-              if (p.partials) {
+              if (STEP) {
                 d2 = fmaf(xn - x, xn - x, d2);
                 x2 = fmaf(xn, xn, x2);
               }
@@ -582,7 +586,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
               const float x = (bf16_to_f32_dev(xr[j]) + bf16_to_f32_dev(xr[p.x_plane_stride + j])) +
                               bf16_to_f32_dev(xr[2 * p.x_plane_stride + j]);
               const float xn = c1 * x + c3 * v[j];
-              if (p.partials) {
+              if (STEP) {
                 d2 = fmaf(xn - x, xn - x, d2);
                 x2 = fmaf(xn, xn, x2);
               }
@@ -643,7 +647,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
       if (lane == 0) p.partials[ctx.part + (warp - 2)] = part;
     }
-    if (EPI == TC_EPI_NS && p.partials) {
+    if (STEP) {
       double a = d2, b = x2;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -834,6 +838,9 @@ cudaError_t dispatch_p(const CUtensorMap& ma, const CUtensorMap& mb, const TcArg
     case TC_EPI_GRAM:
       if (amn && bmn) return launch_t<P, true, true, TC_EPI_GRAM>(ma, mb, a, tm, tn, ntiles, s);
       return cudaErrorInvalidValue;
+    case TC_EPI_NS_STEP:
+      if (!amn && bmn) return launch_t<P, false, true, TC_EPI_NS_STEP>(ma, mb, a, tm, tn, ntiles, s);
+      return cudaErrorInvalidValue;
     case TC_EPI_PLANES:
       if (!amn && bmn) return launch_t<P, false, true, TC_EPI_PLANES>(ma, mb, a, tm, tn, ntiles, s);
       return cudaErrorInvalidValue;
@@ -893,12 +900,13 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
   const TcOperand* ops[2] = {&a.a, &a.b};
   for (const TcOperand* o : ops)
     if (!o->planes || !aligned(o->planes, 16) || o->ld % 8 || o->plane_stride % 8) return cudaErrorInvalidValue;
-  if (a.epi == TC_EPI_NS || a.epi == TC_EPI_GRAM || a.epi == TC_EPI_PLANES) {
+  const bool ns = a.epi == TC_EPI_NS || a.epi == TC_EPI_NS_STEP;
+  if (ns || a.epi == TC_EPI_GRAM || a.epi == TC_EPI_PLANES) {
     if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8) return cudaErrorInvalidValue;
     if (a.out_nplanes < 1 || a.out_nplanes > 3) return cudaErrorInvalidValue;
   }
-  if (a.epi == TC_EPI_GRAM && !a.partials) return cudaErrorInvalidValue;
-  if (a.epi == TC_EPI_NS &&
+  if ((a.epi == TC_EPI_GRAM || a.epi == TC_EPI_NS_STEP) && !a.partials) return cudaErrorInvalidValue;
+  if (ns &&
       (!a.x_planes || !aligned(a.x_planes, 16) || a.ldxp % 8 || a.x_plane_stride % 8 || a.out_nplanes != 3))
     return cudaErrorInvalidValue;
   if (a.triangular && a.M != a.N) return cudaErrorInvalidValue;

@@ -107,7 +107,7 @@ int simt_gram_tiles(int64_t n);
 
 // ---------------------------------------------------------------------------------
 // tcgen05 split-BF16 GEMM / SYRK (gemm_tc.cu)
-enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2, TC_EPI_PLANES = 3 };
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2, TC_EPI_PLANES = 3, TC_EPI_NS_STEP = 4 };
 
 struct TcOperand {
   const uint16_t* planes;  // plane p at planes + p * plane_stride (elements)
@@ -126,7 +126,7 @@ struct TcArgs {
   float* C; int64_t ldc; float alpha, beta;      // STORE
   const uint16_t* x_planes; int64_t ldxp; int64_t x_plane_stride;  // NS: three planes of X_k
   uint16_t* out_planes; int64_t ldo; int64_t out_plane_stride; int out_nplanes; // NS/GRAM plane output
-  double* partials;                               // GRAM residual partials; NS (if set): per tile and warp
+  double* partials;                               // GRAM residual partials; NS_STEP step-size pairs, per tile and warp
                                                   // the pair (sum (x' - x)^2, sum x'^2)
   DevState* st;                                   // skip when not RUNNING; error flags
   int slice_stages;                               // k-stages per promoted slice (0: library default)

@@ -771,6 +771,17 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
                o_part = take((size_t)std::max<int64_t>(2 * npairs, fb) * 8), o_st = take(sizeof(DevState));
   void* ws = nullptr;
   if (cudaMalloc(&ws, off) != cudaSuccess) { cudaGetLastError(); return POLAR_ENOMEM; }
+  int* status_host = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaMallocHost(&status_host, 2 * sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    for (auto e : ev) if (e) cudaEventDestroy(e);
+    if (status_host) cudaFreeHost(status_host);
+    cudaFree(ws);
+    return POLAR_ENOMEM;
+  }
   uint8_t* w = (uint8_t*)ws;
   uint16_t* ap = (uint16_t*)(w + o_a);
   uint16_t* xp[2] = {(uint16_t*)(w + o_x0), (uint16_t*)(w + o_x1)};
@@ -798,8 +809,10 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
     // X_0 = A^T / a; the update X' = 2 X - X (A X)
     if (launch_transpose_scale_split(A, lda, N, M, st, xp[0], lpx, sx, s) != cudaSuccess) break;
     if (launch_inverse_init(st, s) != cudaSuccess) break;
-    bool ok = true;
-    for (int k = 0; k < max_iter && ok; ++k) {
+    // Iterations in chunks of four, two chunks in flight; the host reads the status word
+    // after each chunk and stops enqueueing once the stop rule has fired (kernels enqueued
+    // after that return at once).
+    auto enqueue_iter = [&](int k) {
       TcArgs pa{};  // P = A X_k (N x N, K = M)
       pa.M = N; pa.N = N; pa.K = M;
       pa.a = op_planes(ap, N, M, lpa, sa, 1);
@@ -813,15 +826,32 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
       u.a = op_planes(xp[k & 1], M, N, lpx, sx, 1);
       u.b = op_planes(pp, N, N, lpx, sp, 0);
       u.nplanes = P;
-      u.epi = TC_EPI_NS;
+      u.epi = TC_EPI_NS_STEP;
       u.x_planes = xp[k & 1]; u.ldxp = lpx; u.x_plane_stride = sx;
       u.out_planes = xp[(k + 1) & 1]; u.ldo = lpx; u.out_plane_stride = sx; u.out_nplanes = 3;
       u.partials = part;
       u.st = st;
-      ok = launch_tc_gemm(pa, s) == cudaSuccess && launch_tc_gemm(u, s) == cudaSuccess &&
-           launch_inverse_finalize(part, (int)npairs, st, k, max_iter, s) == cudaSuccess;
+      return launch_tc_gemm(pa, s) == cudaSuccess && launch_tc_gemm(u, s) == cudaSuccess &&
+             launch_inverse_finalize(part, (int)npairs, st, k, max_iter, s) == cudaSuccess;
+    };
+    const int chunk = 4;
+    bool ok = true;
+    int k = 0, head = 0, queued = 0;
+    while (ok) {
+      while (ok && queued < 2 && k < max_iter) {
+        for (int c = 0; c < chunk && k < max_iter && ok; ++c, ++k) ok = enqueue_iter(k);
+        const int slot = (head + queued) & 1;
+        ok = ok && cudaMemcpyAsync(&status_host[slot], &st->status, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+             cudaEventRecord(ev[slot], s) == cudaSuccess;
+        ++queued;
+      }
+      if (!ok || queued == 0) break;
+      ok = cudaEventSynchronize(ev[head]) == cudaSuccess;
+      const int st_now = status_host[head];
+      head ^= 1;
+      --queued;
+      if (st_now != ST_RUNNING) break;
     }
-    if (!ok) break;
     if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) break;
     if (cudaStreamSynchronize(s) != cudaSuccess) break;
     if (h.err_flags || h.status == ST_TIMEOUT) { ret = POLAR_ETIMEOUT; break; }
@@ -833,6 +863,8 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
     ret = h.status == ST_CONVERGED ? POLAR_OK : POLAR_NOT_CONVERGED;
   } while (0);
   cudaStreamSynchronize(s);
+  for (auto e : ev) cudaEventDestroy(e);
+  cudaFreeHost(status_host);
   cudaFree(ws);
   if (ret == POLAR_ECUDA) cudaGetLastError();
   return ret;
