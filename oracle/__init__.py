@@ -13,5 +13,7 @@ Modules:
   precision   bit-level BF16 plane split and an emulator of split products
   ns_inverse  the Newton-Schulz matrix inverse of Algorithm 2 and its trajectory
               predicted from a spectrum
+  chebyshev   Chebyshev interpolation and Clenshaw summation of a matrix function
+              of a symmetric matrix (Eqs. MatFuncEig, EigenvaluePolynomial)
 """
-from . import jacobi_svd, ns_inverse, ns_polar, precision, scalar  # noqa: F401
+from . import chebyshev, jacobi_svd, ns_inverse, ns_polar, precision, scalar  # noqa: F401
