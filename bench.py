@@ -7,7 +7,11 @@ matrix with a prescribed spectrum, input resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload square8192_k1e4] [--prec bf16x6] [--no-plain] [--no-cpu]
-                  [--batched 4096] [--no-precond]
+                  [--batched 4096] [--no-precond] [--no-inverse] [--no-chebyshev]
+
+Beside the headline solve the line carries measured legs on the same shape: the plain FP32
+form, the preconditioned iteration (Algorithm 1), the Newton-Schulz inverse (Algorithm 2),
+a Chebyshev matrix function by Clenshaw summation, and the batched configuration.
 
 Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
 problem of the same size (independent replicas; the single solve does not shard),
@@ -312,6 +316,50 @@ def run_inverse(lib, torch, m, n, seed, stream, peaks, steps, warmup, world, kap
     return out
 
 
+def run_chebyshev(lib, torch, n, seed, stream, peaks, steps, warmup, world, degree=32):
+    """exp(A) by a degree-`degree` Chebyshev series (Clenshaw summation, degree - 1 products)
+    for a symmetric n x n matrix with eigenvalues evenly spread over [-1, 1], drawn on the device.
+    Algorithmic work per call: (degree - 1) products of two symmetric matrices, n^3 each for the
+    upper triangle they need (2 n^3 per product in the paper's convention)."""
+    import numpy as np
+    from paper_2112_09017_gb300 import synth
+    lam = np.linspace(-1.0, 1.0, n)
+    A, (q, lam_t) = synth.symmetric_with_spectrum_on_device(n, lam, seed, "cuda", return_factors=True)
+    coef = lib.chebyshev_coefficients(math.exp, -1.0, 1.0, degree)
+    F = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        lib.polar_chebyshev(A, F, -1.0, 1.0, coef, stream=stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        lib.polar_chebyshev(A, F, -1.0, 1.0, coef, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    products = max(degree - 1, 0)
+    flops = products * float(n) ** 3
+    # sampled entries against Q p(Lambda) Q^T with the generator's float64 factors
+    g = torch.Generator(device="cuda").manual_seed(7)
+    rows = torch.randint(0, n, (256,), device="cuda", generator=g)
+    cols = torch.randint(0, n, (256,), device="cuda", generator=g)
+    p_lam = torch.from_numpy(np.polynomial.chebyshev.chebval(lam, coef)).cuda()
+    want = ((q[rows] * p_lam[None, :]) * q[cols]).sum(dim=1)
+    err = float(torch.max(torch.abs(F[rows, cols].double() - want)))
+    mma = 6.0 * flops / (ms / steps * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained")
+    out = {"value": world * flops * steps / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms / steps,
+           "n": n, "degree": degree, "products": products, "function": "exp on [-1, 1]",
+           "paper_convention_tflops": world * 2.0 * flops * steps / (ms * 1e-3) / 1e12,
+           "max_abs_err_sampled": err, "bf16_mma_tflops": mma,
+           "tensor_frac_of_measured_sustained": (mma / peak) if peak else None,
+           "note": "whole call (workspace, set-up, products, output) per step; flops = (degree - 1) n^3 for the "
+                   "upper triangles; bf16_mma_tflops counts the six split passes"}
+    del A, F, q
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -470,6 +518,12 @@ def run_ours(args):
         inverse = run_inverse(lib, torch, m, n, w.seed + 1000 + rank, stream, peaks, max(1, min(args.steps, 3)),
                               min(args.warmup, 3), world)
 
+    # ---- Chebyshev matrix function (Clenshaw) on a symmetric matrix of the same size ----
+    cheb = None
+    if not args.no_chebyshev:
+        cheb = run_chebyshev(lib, torch, n, w.seed + 2000 + rank, stream, peaks, max(1, min(args.steps, 3)),
+                             min(args.warmup, 3), world)
+
     # ---- batched configuration beside the single solve ----
     batched = None
     if args.batched > 0:
@@ -503,6 +557,7 @@ def run_ours(args):
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "batched": batched, "preconditioned": pre, "ns_inverse": inverse,
+            "chebyshev": cheb,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -524,6 +579,7 @@ def main():
     ap.add_argument("--batched", type=int, default=4096, help="problems in the batched leg (0: skip)")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned (Algorithm 1) leg")
     ap.add_argument("--no-inverse", action="store_true", help="skip the Newton-Schulz inverse (Algorithm 2) leg")
+    ap.add_argument("--no-chebyshev", action="store_true", help="skip the Chebyshev / Clenshaw leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

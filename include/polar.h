@@ -185,6 +185,31 @@ POLAR_API polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t 
                                           int64_t ldx, int prec, int max_iter, int32_t* iters, double* delta,
                                           polar_stream_t stream);
 
+/* The degree + 1 first-kind Chebyshev points of [a, b] (b > a, degree >= 0), host memory:
+ * x[j] = (a + b)/2 + (b - a)/2 cos(pi (j + 1/2) / (degree + 1)), j = 0..degree.
+ * Paper: Sec. III.D, the matrix-function paragraph after Algorithm 2. Returns OK or EINVAL. */
+POLAR_API polar_status_t polar_chebyshev_nodes(double a, double b, int degree, double* x);
+
+/* Coefficients c_0..c_degree of the Chebyshev interpolant through g[j] = g(x[j]) at the points of
+ * polar_chebyshev_nodes (host memory): c_k = 2/(degree + 1) sum_j g[j] cos(k pi (j + 1/2)/(degree + 1)),
+ * c_0 halved, so that p(x) = sum_k c_k T_k((2x - a - b)/(b - a)). Returns OK, EINVAL or ENONFINITE. */
+POLAR_API polar_status_t polar_chebyshev_fit(const double* g, int degree, double* coef);
+
+/* Chebyshev matrix function F = sum_k coef[k] T_k(T), T = (2A - (a + b) I)/(b - a), of a real symmetric
+ * n x n matrix A whose eigenvalues lie in [a, b] (the matrix function of Eq. MatFuncEig through the
+ * polynomial of Eq. EigenvaluePolynomial), by Clenshaw summation:
+ *   B_{d+1} = B_{d+2} = 0, B_k = c_k I + 2 T B_{k+1} - B_{k+2} (k = d..1), F = c_0 I + T B_1 - B_2,
+ * degree - 1 matrix products for degree >= 2 on the tensor cores (split BF16 as polar_run; each product
+ * of two polynomials in T is symmetric, so only its upper-triangle tiles are computed and mirrored).
+ * Only the upper triangle of A (lda >= n) is read; F (ldf >= n) is written in full and is exactly
+ * symmetric. A and F are device pointers, coef host memory (degree + 1 finite values, rounded to
+ * float32 where they enter the device arithmetic). prec: BF16X6, BF16X3 or BF16; FP32 -> ENOTSUP.
+ * Allocates its workspace for the call and returns after F is written. Returns OK, EINVAL, ENOMEM,
+ * ENOTSUP, ETIMEOUT or ECUDA. Paper: Sec. III.D, the matrix-function paragraph after Algorithm 2. */
+POLAR_API polar_status_t polar_chebyshev(const float* A, int64_t n, int64_t lda, double a, double b,
+                                         const double* coef, int degree, float* F, int64_t ldf, int prec,
+                                         polar_stream_t stream);
+
 /* Size of the static device array behind polar_gemm_noalloc (32 MiB). */
 #define POLAR_NOALLOC_SCRATCH_BYTES (32u << 20)
 

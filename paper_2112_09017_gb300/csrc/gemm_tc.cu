@@ -29,6 +29,9 @@
 //                 NS     X_{k+1} = c1 X_k + c3 acc (1.5, -0.5, or the preconditioning
 //                        coefficients of Algorithm 1), X_k read from its three
 //                        BF16 planes (an exact FP32 encoding), written as planes
+//                 CLENSHAW alpha acc + beta Z + diag I on the upper-triangle tiles,
+//                        each entry also stored at its mirror position (a product of
+//                        two commuting symmetric matrices), Z read from three planes
 //                 NS_STEP NS, plus float64 per-warp sums of (X_{k+1} - X_k)^2 and
 //                        X_{k+1}^2 (the step size of the inverse iteration)
 //                 PLANES the product itself as BF16 planes (an operand of the next product)
@@ -508,6 +511,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     const int64_t nslices = (ctx.nk + SL - 1) / SL;
     constexpr bool NS = EPI == TC_EPI_NS || EPI == TC_EPI_NS_STEP;
     constexpr bool STEP = EPI == TC_EPI_NS_STEP;
+    constexpr bool CLEN = EPI == TC_EPI_CLENSHAW;
     float acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
@@ -525,8 +529,8 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       __syncwarp();
       if (lane == 0) mbar_arrive(br.tempty0 + 8 * buf);
       if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
-      if (NS && sl == (nslices > 1 ? nslices - 2 : 0)) {
-        // the output step reads this row's 128 columns of X_k's three planes: pull them into L2 now
+      if ((NS || CLEN) && sl == (nslices > 1 ? nslices - 2 : 0)) {
+        // the output step reads this row's 128 columns of X_k's (or Z's) three planes: pull them into L2 now
         const int64_t r = ctx.bi * BM + row_in_tile;
         const int64_t c0 = ctx.bj * BN + half * 128;
         if (r < p.M && c0 < p.N) {
@@ -620,6 +624,41 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
           }
         }
         part += 2.0 * (double)s_off + (double)s_diag;
+      } else if (CLEN) {
+        // Clenshaw step on the upper triangle, mirrored: alpha acc + beta Z + diag I, Z from its three planes
+        const uint16_t* zr = p.x_planes + r * p.ldxp + c0;
+        uint16_t* pr = p.out_planes + r * p.ldo + c0;
+        uint16_t* pt = p.out_planes + c0 * p.ldo + r;
+        if (full_chunk && r < c0) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint4 h = *reinterpret_cast<const uint4*>(zr + 8 * i);
+            uint4 m = *reinterpret_cast<const uint4*>(zr + p.x_plane_stride + 8 * i);
+            uint4 l = *reinterpret_cast<const uint4*>(zr + 2 * p.x_plane_stride + 8 * i);
+            const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, mw[4] = {m.x, m.y, m.z, m.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int w = e >> 1, sh = (e & 1) * 16;
+              const float z = (bf16_to_f32_dev((uint16_t)(hw[w] >> sh)) + bf16_to_f32_dev((uint16_t)(mw[w] >> sh))) +
+                              bf16_to_f32_dev((uint16_t)(lw[w] >> sh));
+              v[8 * i + e] = fmaf(p.alpha, v[8 * i + e], p.beta * z);
+            }
+          }
+          store_planes32_mirror(pr, pt, p.ldo, p.out_plane_stride, p.out_nplanes, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t cc = c0 + j;
+            if (cc < p.N && r <= cc) {
+              const float z = (bf16_to_f32_dev(zr[j]) + bf16_to_f32_dev(zr[p.x_plane_stride + j])) +
+                              bf16_to_f32_dev(zr[2 * p.x_plane_stride + j]);
+              float o = fmaf(p.alpha, v[j], p.beta * z);
+              if (r == cc) o += p.diag;
+              else store_planes1(pt + j * p.ldo, p.out_plane_stride, p.out_nplanes, o);
+              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, o);
+            }
+          }
+        }
       } else if (EPI == TC_EPI_PLANES) {
         // the product itself as three BF16 planes (an operand of the next product)
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
@@ -841,6 +880,9 @@ cudaError_t dispatch_p(const CUtensorMap& ma, const CUtensorMap& mb, const TcArg
     case TC_EPI_NS_STEP:
       if (!amn && bmn) return launch_t<P, false, true, TC_EPI_NS_STEP>(ma, mb, a, tm, tn, ntiles, s);
       return cudaErrorInvalidValue;
+    case TC_EPI_CLENSHAW:
+      if (amn && bmn) return launch_t<P, true, true, TC_EPI_CLENSHAW>(ma, mb, a, tm, tn, ntiles, s);
+      return cudaErrorInvalidValue;
     case TC_EPI_PLANES:
       if (!amn && bmn) return launch_t<P, false, true, TC_EPI_PLANES>(ma, mb, a, tm, tn, ntiles, s);
       return cudaErrorInvalidValue;
@@ -901,12 +943,14 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
   for (const TcOperand* o : ops)
     if (!o->planes || !aligned(o->planes, 16) || o->ld % 8 || o->plane_stride % 8) return cudaErrorInvalidValue;
   const bool ns = a.epi == TC_EPI_NS || a.epi == TC_EPI_NS_STEP;
-  if (ns || a.epi == TC_EPI_GRAM || a.epi == TC_EPI_PLANES) {
+  const bool clen = a.epi == TC_EPI_CLENSHAW;
+  if (ns || clen || a.epi == TC_EPI_GRAM || a.epi == TC_EPI_PLANES) {
     if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8) return cudaErrorInvalidValue;
     if (a.out_nplanes < 1 || a.out_nplanes > 3) return cudaErrorInvalidValue;
   }
   if ((a.epi == TC_EPI_GRAM || a.epi == TC_EPI_NS_STEP) && !a.partials) return cudaErrorInvalidValue;
-  if (ns &&
+  if (clen && (!a.triangular || a.M != a.N)) return cudaErrorInvalidValue;
+  if ((ns || clen) &&
       (!a.x_planes || !aligned(a.x_planes, 16) || a.ldxp % 8 || a.x_plane_stride % 8 || a.out_nplanes != 3))
     return cudaErrorInvalidValue;
   if (a.triangular && a.M != a.N) return cudaErrorInvalidValue;

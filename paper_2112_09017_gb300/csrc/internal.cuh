@@ -86,6 +86,11 @@ cudaError_t launch_inverse_finalize(const double* partials, int npairs, DevState
 // dst = plane_0 + plane_1 + plane_2 (the FP32 value the three BF16 planes encode exactly)
 cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
                                  float* dst, int64_t ldd, cudaStream_t s);
+// Clenshaw set-up (n x n): planes of s1 (alpha_map S + beta_map I) + s0 I, S the symmetric matrix
+// whose upper triangle is A's, each value rounded once to float32 and split into `nplanes` planes.
+cudaError_t launch_cheb_affine_split(const float* A, int64_t lda, int64_t n, double alpha_map, double beta_map,
+                                     double s1, double s0, uint16_t* planes, int64_t ldp, int64_t plane_stride,
+                                     int nplanes, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // SIMT float32 GEMM / SYRK (gemm_simt.cu)
@@ -107,7 +112,8 @@ int simt_gram_tiles(int64_t n);
 
 // ---------------------------------------------------------------------------------
 // tcgen05 split-BF16 GEMM / SYRK (gemm_tc.cu)
-enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2, TC_EPI_PLANES = 3, TC_EPI_NS_STEP = 4 };
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_NS = 1, TC_EPI_GRAM = 2, TC_EPI_PLANES = 3, TC_EPI_NS_STEP = 4,
+                   TC_EPI_CLENSHAW = 5 };
 
 struct TcOperand {
   const uint16_t* planes;  // plane p at planes + p * plane_stride (elements)
@@ -123,8 +129,9 @@ struct TcArgs {
   int nplanes;             // 1..3: planes stored per operand (and passes: 1, 3, 6)
   int epi;                 // TcEpi
   int triangular;          // SYRK upper-triangle tiles + mirror store
-  float* C; int64_t ldc; float alpha, beta;      // STORE
-  const uint16_t* x_planes; int64_t ldxp; int64_t x_plane_stride;  // NS: three planes of X_k
+  float* C; int64_t ldc; float alpha, beta;      // STORE; CLENSHAW: alpha acc + beta Z + diag I
+  float diag;                                     // CLENSHAW: added on the diagonal
+  const uint16_t* x_planes; int64_t ldxp; int64_t x_plane_stride;  // NS: three planes of X_k; CLENSHAW: of Z
   uint16_t* out_planes; int64_t ldo; int64_t out_plane_stride; int out_nplanes; // NS/GRAM plane output
   double* partials;                               // GRAM residual partials; NS_STEP step-size pairs, per tile and warp
                                                   // the pair (sum (x' - x)^2, sum x'^2)

@@ -280,6 +280,44 @@ __global__ void transpose_scale_split_kernel(const float* __restrict__ A, int64_
   }
 }
 
+// Clenshaw set-up: out(i, j) = s1 (alpha_map S(i, j) + beta_map [i = j]) + s0 [i = j], with S the
+// symmetric matrix whose upper triangle is A's. Each 32 x 32 output tile reads the upper-triangle
+// tile that holds its entries (itself above the diagonal, its transpose below) through shared memory.
+__global__ void cheb_affine_split_kernel(const float* __restrict__ A, int64_t lda, int64_t n, double am, double bm,
+                                         double s1, double s0, uint16_t* __restrict__ P, int64_t ldp, int64_t ps,
+                                         int nplanes) {
+  __shared__ float t[32][33];
+  const int64_t nt = (n + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t b = blockIdx.x; b < nt * nt; b += gridDim.x) {
+    const int64_t bi = b / nt, bj = b % nt;
+    const int64_t si = bi < bj ? bi : bj, sj = bi < bj ? bj : bi;  // source tile in the upper triangle
+    __syncthreads();
+    if (s1 != 0.0) {
+      for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t r = si * 32 + yy, c = sj * 32 + tx;
+        t[yy][tx] = (r < n && c < n) ? A[r * lda + c] : 0.0f;
+      }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+      const int64_t i = bi * 32 + yy, j = bj * 32 + tx;
+      if (i >= n || j >= n) continue;
+      // entry (i, j) of S: A(min, max); within the source tile at (yy, tx) or transposed
+      const bool upper = bi < bj || (bi == bj && yy <= tx);
+      const double a = s1 != 0.0 ? (double)(upper ? t[yy][tx] : t[tx][yy]) : 0.0;
+      const bool d = i == j;
+      const float v = (float)(s1 * (am * a + (d ? bm : 0.0)) + (d ? s0 : 0.0));
+      float rem = v;
+      for (int q = 0; q < nplanes; ++q) {
+        const uint16_t bq = bf16_rne_bits(rem);
+        P[q * ps + i * ldp + j] = bq;
+        rem = rem - bf16_bits_to_float(bq);
+      }
+    }
+  }
+}
+
 __global__ void inverse_init_kernel(DevState* st) {
   st->upd_c1 = 2.0f;   // X' = X (2I - A X) = 2 X - X (A X)
   st->upd_c3 = -1.0f;
@@ -410,6 +448,15 @@ cudaError_t launch_transpose_scale_split(const float* A, int64_t lda, int64_t ro
   const int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
   transpose_scale_split_kernel<<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(A, lda, rows, cols, st, planes,
                                                                                        ldp, plane_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_affine_split(const float* A, int64_t lda, int64_t n, double alpha_map, double beta_map,
+                                     double s1, double s0, uint16_t* planes, int64_t ldp, int64_t plane_stride,
+                                     int nplanes, cudaStream_t s) {
+  const int64_t tiles = ((n + 31) / 32) * ((n + 31) / 32);
+  cheb_affine_split_kernel<<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(
+      A, lda, n, alpha_map, beta_map, s1, s0, planes, ldp, plane_stride, nplanes);
   return cudaGetLastError();
 }
 

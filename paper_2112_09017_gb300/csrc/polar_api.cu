@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -865,6 +866,98 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
   cudaStreamSynchronize(s);
   for (auto e : ev) cudaEventDestroy(e);
   cudaFreeHost(status_host);
+  cudaFree(ws);
+  if (ret == POLAR_ECUDA) cudaGetLastError();
+  return ret;
+}
+
+extern "C" polar_status_t polar_chebyshev_nodes(double a, double b, int degree, double* x) {
+  if (!x || degree < 0 || !std::isfinite(a) || !std::isfinite(b) || !(b > a)) return POLAR_EINVAL;
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j <= degree; ++j) x[j] = 0.5 * (a + b) + 0.5 * (b - a) * std::cos(pi * (j + 0.5) / (degree + 1));
+  return POLAR_OK;
+}
+
+extern "C" polar_status_t polar_chebyshev_fit(const double* g, int degree, double* coef) {
+  if (!g || !coef || degree < 0) return POLAR_EINVAL;
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j <= degree; ++j)
+    if (!std::isfinite(g[j])) return POLAR_ENONFINITE;
+  for (int k = 0; k <= degree; ++k) {
+    double acc = 0.0;
+    for (int j = 0; j <= degree; ++j) acc += g[j] * std::cos(k * pi * (j + 0.5) / (degree + 1));
+    coef[k] = 2.0 * acc / (degree + 1);
+  }
+  coef[0] *= 0.5;
+  return POLAR_OK;
+}
+
+extern "C" polar_status_t polar_chebyshev(const float* A, int64_t n, int64_t lda, double a, double b,
+                                          const double* coef, int degree, float* F, int64_t ldf, int prec,
+                                          polar_stream_t stream) {
+  if (!A || !F || !coef || n < 1 || lda < n || ldf < n || degree < 0) return POLAR_EINVAL;
+  if (!std::isfinite(a) || !std::isfinite(b) || !(b > a)) return POLAR_EINVAL;
+  for (int k = 0; k <= degree; ++k)
+    if (!std::isfinite(coef[k])) return POLAR_EINVAL;
+  if (overlaps(A, (size_t)((n - 1) * lda + n) * 4, F, (size_t)((n - 1) * ldf + n) * 4)) return POLAR_EINVAL;
+  if (prec == POLAR_AUTO) prec = POLAR_BF16X6;
+  const int P = planes_of(prec);
+  if (prec == POLAR_SCHED_BF16_THEN_X3 || P == 0) return prec == POLAR_FP32 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  if (!tc_available()) return POLAR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double am = 2.0 / (b - a), bm = -(a + b) / (b - a);   // T = am A + bm I
+  // workspace: T planes (P), three rotating B_k buffers (three planes each: they are also read
+  // as Z = B_{k+2} by the epilogue), device state
+  const int64_t ldp = round_up(n, 64), sp = round_up(n * ldp, 64);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t o_t = take((size_t)P * sp * 2), o_b0 = take((size_t)3 * sp * 2), o_b1 = take((size_t)3 * sp * 2),
+               o_b2 = take((size_t)3 * sp * 2), o_st = take(sizeof(DevState));
+  void* ws = nullptr;
+  if (cudaMalloc(&ws, off) != cudaSuccess) { cudaGetLastError(); return POLAR_ENOMEM; }
+  uint8_t* w = (uint8_t*)ws;
+  uint16_t* tp = (uint16_t*)(w + o_t);
+  uint16_t* bk[3] = {(uint16_t*)(w + o_b0), (uint16_t*)(w + o_b1), (uint16_t*)(w + o_b2)};
+  DevState* st = (DevState*)(w + o_st);
+  polar_status_t ret = POLAR_ECUDA;
+  do {
+    if (cudaMemsetAsync(ws, 0, off, s) != cudaSuccess) break;   // also status = RUNNING
+    bool ok = true;
+    if (degree <= 1) {
+      // F = c_0 I + c_1 T: no product
+      ok = launch_cheb_affine_split(A, lda, n, am, bm, degree == 1 ? coef[1] : 0.0, coef[0], bk[0], ldp, sp, 3, s) ==
+           cudaSuccess;
+    } else {
+      const int d = degree;
+      ok = launch_cheb_affine_split(A, lda, n, am, bm, 1.0, 0.0, tp, ldp, sp, P, s) == cudaSuccess &&
+           // B_d = c_d I and B_{d-1} = c_{d-1} I + 2 c_d T need no product
+           launch_cheb_affine_split(A, lda, n, am, bm, 0.0, coef[d], bk[d % 3], ldp, sp, 3, s) == cudaSuccess &&
+           launch_cheb_affine_split(A, lda, n, am, bm, 2.0 * coef[d], coef[d - 1], bk[(d - 1) % 3], ldp, sp, 3, s) ==
+               cudaSuccess;
+      // B_k = 2 T B_{k+1} - B_{k+2} + c_k I for k = d-2..1, then F = T B_1 - B_2 + c_0 I (into B_0's slot)
+      for (int k = d - 2; k >= 0 && ok; --k) {
+        TcArgs g{};
+        g.M = n; g.N = n; g.K = n;
+        g.a = op_planes(tp, n, n, ldp, sp, 0);               // T is symmetric: its K x M view is itself
+        g.b = op_planes(bk[(k + 1) % 3], n, n, ldp, sp, 0);
+        g.nplanes = P;
+        g.epi = TC_EPI_CLENSHAW; g.triangular = 1;
+        g.alpha = k > 0 ? 2.0f : 1.0f; g.beta = -1.0f; g.diag = (float)coef[k];
+        g.x_planes = bk[(k + 2) % 3]; g.ldxp = ldp; g.x_plane_stride = sp;
+        g.out_planes = bk[k % 3]; g.ldo = ldp; g.out_plane_stride = sp; g.out_nplanes = 3;
+        g.st = st;
+        ok = launch_tc_gemm(g, s) == cudaSuccess;
+      }
+    }
+    if (!ok) break;
+    if (launch_planes_to_f32(bk[0], ldp, sp, n, n, F, ldf, s) != cudaSuccess) break;
+    DevState h;
+    if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) break;
+    ret = (h.err_flags || h.status == ST_TIMEOUT) ? POLAR_ETIMEOUT : POLAR_OK;
+  } while (0);
+  cudaStreamSynchronize(s);
   cudaFree(ws);
   if (ret == POLAR_ECUDA) cudaGetLastError();
   return ret;

@@ -82,6 +82,9 @@ def load():
         "polar_syrk": (i32, [i64, i64, f32, vp, i64, f32, vp, i64, i32, vp]),
         "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
         "polar_ns_inverse": (i32, [vp, i64, i64, i64, vp, i64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
+        "polar_chebyshev_nodes": (i32, [f64, f64, i32, C.POINTER(f64)]),
+        "polar_chebyshev_fit": (i32, [C.POINTER(f64), i32, C.POINTER(f64)]),
+        "polar_chebyshev": (i32, [vp, i64, i64, f64, f64, C.POINTER(f64), i32, vp, i64, i32, vp]),
         "polar_device_query": (i32, [C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
@@ -238,6 +241,46 @@ def polar_ns_inverse(A, X, prec=POLAR_BF16X6, max_iter=100, stream=None, raw_sta
     if not raw_status and r not in (POLAR_OK, POLAR_NOT_CONVERGED):
         raise PolarError(r, "polar_ns_inverse")
     return {"status": r, "iters": it.value, "delta": d.value}
+
+
+def polar_chebyshev_nodes(a, b, degree):
+    """The degree + 1 first-kind Chebyshev points of [a, b] (a list of floats)."""
+    x = (C.c_double * (degree + 1))()
+    r = load().polar_chebyshev_nodes(float(a), float(b), int(degree), x)
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_chebyshev_nodes")
+    return list(x)
+
+
+def polar_chebyshev_fit(g_at_nodes):
+    """Chebyshev coefficients c_0..c_d of the interpolant through the values at the nodes."""
+    d = len(g_at_nodes) - 1
+    g = (C.c_double * (d + 1))(*[float(v) for v in g_at_nodes])
+    c = (C.c_double * (d + 1))()
+    r = load().polar_chebyshev_fit(g, d, c)
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_chebyshev_fit")
+    return list(c)
+
+
+def chebyshev_coefficients(g, a, b, degree):
+    """Coefficients of the degree-`degree` Chebyshev interpolant of the scalar function g on [a, b]."""
+    return polar_chebyshev_fit([g(x) for x in polar_chebyshev_nodes(a, b, degree)])
+
+
+def polar_chebyshev(A, F, a, b, coef, prec=POLAR_BF16X6, stream=None, raw_status=False):
+    """F = sum_k coef[k] T_k((2A - (a + b) I)/(b - a)) for a symmetric device tensor A (upper triangle
+    read), by Clenshaw summation on the tensor cores. Returns the status."""
+    _check_f32_2d(A, "A"); _check_f32_2d(F, "F")
+    n = A.shape[0]
+    if A.shape[1] != n or tuple(F.shape) != (n, n):
+        raise ValueError("A and F must be n x n")
+    cf = (C.c_double * len(coef))(*[float(v) for v in coef])
+    r = load().polar_chebyshev(_ptr(A), n, A.stride(0), float(a), float(b), cf, len(coef) - 1, _ptr(F),
+                               F.stride(0), int(prec), _stream(stream))
+    if not raw_status and r != POLAR_OK:
+        raise PolarError(r, "polar_chebyshev")
+    return r
 
 
 def polar_split_bf16(X, planes: int, stream=None):

@@ -193,3 +193,22 @@ def matrix_with_spectrum_on_device(m: int, n: int, sigma: np.ndarray, seed: int,
     if return_factors:
         return a, (q1, s, q2)
     return a
+
+
+def symmetric_with_spectrum_on_device(n: int, lam: np.ndarray, seed: int, device, return_factors: bool = False):
+    """A = fl32(sym(Q diag(lam) Q^T)) with Q Haar-distributed (sign-fixed QR of a float64 Gaussian
+    drawn from torch's generator seeded with `seed`, on the device): the input of the Chebyshev
+    matrix-function workloads, eigenvalues `lam` up to the float32 rounding of A."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    q, r = torch.linalg.qr(torch.randn(n, n, device=device, generator=g, dtype=torch.float64))
+    d = torch.sign(torch.diagonal(r))
+    d[d == 0] = 1.0
+    q = q * d[None, :]
+    lam_t = torch.from_numpy(np.asarray(lam, dtype=np.float64)).to(device=device)
+    m = (q * lam_t[None, :]) @ q.T
+    a = (0.5 * (m + m.T)).to(torch.float32).contiguous()
+    if return_factors:
+        return a, (q, lam_t)
+    del m
+    return a

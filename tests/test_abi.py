@@ -79,3 +79,25 @@ def test_no_cpu_fallback_in_product_sources():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_chebyshev_host_setup_matches_oracle(built_lib):
+    """The library's Chebyshev points and interpolation coefficients (host C code) against the
+    oracle's; no device work."""
+    import numpy as np
+    from oracle.chebyshev import chebyshev_fit, chebyshev_nodes
+    from paper_2112_09017_gb300 import polar
+    for a, b, d in [(-1.0, 1.0, 0), (-2.0, 3.0, 7), (0.01, 1.0, 40)]:
+        x = np.array(polar.polar_chebyshev_nodes(a, b, d))
+        assert np.max(np.abs(x - chebyshev_nodes(a, b, d))) <= 1e-14 * max(abs(a), abs(b))
+        g = np.exp(-x) / np.sqrt(x + 3.0)
+        c = np.array(polar.polar_chebyshev_fit(list(g)))
+        assert np.max(np.abs(c - chebyshev_fit(g))) <= 1e-14
+    lib = polar.load()
+    out = (ctypes.c_double * 4)()
+    assert lib.polar_chebyshev_nodes(1.0, 1.0, 3, out) == polar.POLAR_EINVAL          # empty interval
+    assert lib.polar_chebyshev_nodes(0.0, 1.0, -1, out) == polar.POLAR_EINVAL
+    bad = (ctypes.c_double * 2)(1.0, float("nan"))
+    assert lib.polar_chebyshev_fit(bad, 1, out) == polar.POLAR_ENONFINITE
+    coef = (ctypes.c_double * 2)(1.0, 2.0)
+    assert lib.polar_chebyshev(None, 4, 4, -1.0, 1.0, coef, 1, None, 4, 1, None) == polar.POLAR_EINVAL
