@@ -85,6 +85,10 @@ typedef struct {
                               s_minus under Eq. RogueScalar; then Newton-Schulz. Stop tests start after them */
   double s_minus;          /* preconditioning threshold; <= 0 means 0.1 */
   double s0;               /* estimate of the smallest singular value of A / ||A||_F; <= 0 means 2^-23 */
+  int small_onchip;        /* batched plans with a fixed plane count: nonzero (the default) solves every
+                              problem with n <= 128 and m <= 256 in one CTA that keeps X, G and the
+                              accumulators on its SM for the whole loop; 0 sends them through the
+                              grouped tile kernels like the others */
 } polar_options_t;
 
 #define POLAR_HIST 128

@@ -20,6 +20,7 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
+#include "stop_rule.cuh"
 
 namespace polar {
 
@@ -136,25 +137,9 @@ __global__ void b_finalize_kernel(const BMeta* __restrict__ meta, DevState* __re
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane != 0) return;
   const double r = sqrt(acc) * s.inv_sqrt_n;
-  if (k < POLAR_HIST) {
-    s.res_hist[k] = r;
-    s.planes_hist[k] = (unsigned char)s.planes_next;
-    s.hist_len = k + 1;
-  }
-  const double r2 = (k >= 2) ? s.ring[(k - 2) & 3] : 0.0;
-  s.ring[k & 3] = r;
-  s.iters = k;
   const double tol = sh->tol > 0 ? sh->tol : rule.tol;
-  const bool testing = k >= rule.n_pre;  // Algorithm 1: no stop test during preconditioning
-  if (!isfinite(r)) s.status = ST_NONFINITE;
-  else if (testing && r <= tol) s.status = ST_CONVERGED;
-  else if (testing && k >= rule.n_pre + 2 && r > rule.stagnation * r2 && r < rule.stag_floor)
-    s.status = ST_NOT_CONVERGED;
-  else if (k >= rule.max_iter) s.status = ST_NOT_CONVERGED;
-  else {
+  if (batched_step_rule(s, rule, tol, r, k, s.planes_next)) {
     s.planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
-    s.upd_c1 = k < rule.n_pre ? (float)rule.pre_a : 1.5f;
-    s.upd_c3 = k < rule.n_pre ? (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a) : -0.5f;
     atomicAdd(&sh->running[k < POLAR_HIST + 8 ? k : POLAR_HIST + 7], 1);
   }
 }
@@ -268,6 +253,8 @@ struct BatchedPlan {
   TcTile* upd_t = nullptr;
   TcTile* h_t = nullptr;
   int64_t n_gram_t = 0, n_upd_t = 0, n_h_t = 0;
+  OcTask* oc_tasks = nullptr;      // problems solved on one SM each (largest first)
+  int n_oc = 0;
   int32_t* iters_scratch = nullptr;
   double* resid_scratch = nullptr;
   cudaStream_t cap = nullptr;
@@ -338,6 +325,8 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   BK_(cudaGetLastError());
   b_scale_split_kernel<<<dim3(count, 16), kThreads, 0, s>>>(b->A_tab, b->meta_d, b->st_d, b->P);
   BK_(cudaGetLastError());
+  // the small problems' whole loops, one SM each; the grouped launches below skip them
+  BK_(launch_onchip_ns(b->oc_tasks, b->n_oc, rule, &b->sh_d->tol, &b->sh_d->err, b->P, s));
   for (int k = 0; k <= b->opt.max_iter; ++k) {
     TcGroupLaunch g{};
     g.nplanes = b->P;
@@ -418,9 +407,14 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return (double)m[x] * n[x] * n[x] > (double)m[y] * n[y] * n[y]; });
+  // problems that fit one SM run their loop there (fixed plane counts only); the rest go
+  // through the grouped tile kernels, which all problems share for H
+  const bool oc_ok = opt.small_onchip != 0 && prec != POLAR_SCHED_BF16_THEN_X3;
+  std::vector<int> order_tc, order_oc;
+  for (int p : order) (oc_ok && onchip_fits(m[p], n[p]) ? order_oc : order_tc).push_back(p);
   std::vector<TcTile> gram_t, upd_t, h_t;
-  build_tiles(order, b->n, b->n, true, gram_t, &ntg);
-  build_tiles(order, b->m, b->n, false, upd_t, nullptr);
+  build_tiles(order_tc, b->n, b->n, true, gram_t, &ntg);
+  build_tiles(order_tc, b->m, b->n, false, upd_t, nullptr);
   build_tiles(order, b->n, b->n, false, h_t, nullptr);
   size_t part_count = 0;
   for (int p = 0; p < count; ++p) part_count += (size_t)ntg[p] * kEpiWarps;
@@ -464,6 +458,23 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   if ((r = b_alloc(b, sizeof(DevState) * count, &v)) != POLAR_OK) return fail(r);
   b->st_d = (DevState*)v;
   if (cudaMemset(v, 0, sizeof(DevState) * count) != cudaSuccess) return fail(POLAR_ECUDA);
+  if (!order_oc.empty()) {
+    std::vector<OcTask> tasks;
+    for (int p : order_oc) {
+      OcTask t;
+      t.m = meta[p].m; t.n = meta[p].n; t.ldp = meta[p].ldp; t.xps = meta[p].xps;
+      t.x0 = meta[p].xp[0];
+      t.xp[0] = meta[p].xp[0];
+      t.xp[1] = meta[p].xp[1];
+      t.st = b->st_d + p;
+      tasks.push_back(t);
+    }
+    if ((r = b_alloc(b, sizeof(OcTask) * tasks.size(), &v)) != POLAR_OK) return fail(r);
+    b->oc_tasks = (OcTask*)v;
+    b->n_oc = (int)tasks.size();
+    if (cudaMemcpy(v, tasks.data(), sizeof(OcTask) * tasks.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(POLAR_ECUDA);
+  }
   if ((r = b_alloc(b, sizeof(BShared), &v)) != POLAR_OK) return fail(r);
   b->sh_d = (BShared*)v;
   if (cudaMemset(v, 0, sizeof(BShared)) != cudaSuccess) return fail(POLAR_ECUDA);

@@ -49,6 +49,19 @@ struct StopRule {
 // Number of Eq. RogueScalar steps lifting s0 to s_minus (the first loop of Algorithm 1).
 int precond_steps(double s_minus, double s0);
 
+// Small batched problems solved on one SM each (onchip.cu): X_0's three planes at x0
+// (pitch ldp, plane stride xps, as the batched workspace stores them); the final
+// iterate's planes go to xp[iters & 1]; the stop rule updates *st.
+struct OcTask {
+  int64_t m, n, ldp, xps;
+  const uint16_t* x0;
+  uint16_t* xp[2];
+  DevState* st;
+};
+bool onchip_fits(int64_t m, int64_t n);   // n <= 128, n <= m <= 256
+cudaError_t launch_onchip_ns(const OcTask* tasks, int ntasks, const StopRule& rule, const double* tol_dev,
+                             int* err_word, int P, cudaStream_t s);
+
 // ---------------------------------------------------------------------------------
 // Misc kernels (kernels_misc.cu)
 // Frobenius norm: per-block float64 partials, then a fixed-order final sum.

@@ -140,6 +140,7 @@ void polar_default_options(polar_options_t* o) {
   o->precondition = 0;
   o->s_minus = 0.1;
   o->s0 = 0.0;
+  o->small_onchip = 1;
 }
 
 const char* polar_status_string(polar_status_t s) {
