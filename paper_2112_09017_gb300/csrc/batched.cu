@@ -138,7 +138,8 @@ __global__ void b_finalize_kernel(const BMeta* __restrict__ meta, DevState* __re
   if (lane != 0) return;
   const double r = sqrt(acc) * s.inv_sqrt_n;
   const double tol = sh->tol > 0 ? sh->tol : rule.tol;
-  if (batched_step_rule(s, rule, tol, r, k, s.planes_next)) {
+  float c1, c3;
+  if (batched_step_rule(s, rule, tol, r, k >= 2 ? s.ring[(k - 2) & 3] : 0.0, k, s.planes_next, c1, c3)) {
     s.planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
     atomicAdd(&sh->running[k < POLAR_HIST + 8 ? k : POLAR_HIST + 7], 1);
   }
@@ -327,7 +328,8 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   BK_(cudaGetLastError());
   // the small problems' whole loops, one SM each; the grouped launches below skip them
   BK_(launch_onchip_ns(b->oc_tasks, b->n_oc, rule, &b->sh_d->tol, &b->sh_d->err, b->P, s));
-  for (int k = 0; k <= b->opt.max_iter; ++k) {
+  // the grouped loop, unless every problem was solved on-chip
+  for (int k = 0; k <= b->opt.max_iter && b->n_gram_t > 0; ++k) {
     TcGroupLaunch g{};
     g.nplanes = b->P;
     g.epi = TC_EPI_GRAM; g.a_mn = 1; g.b_mn = 1;

@@ -18,10 +18,10 @@
 //                  columns of X), B = X, N = the rows of X; then
 //                  X_{k+1}(r, i) = c1 X_k(r, i) + c3 P^T(i, r), split back into the
 //                  planes in place
-// Warps 0-7 (workers, two per TMEM lane quarter, one per half of the columns) load
-// X_0, promote accumulators, evaluate the residual and the stop rule, write G into
-// TMEM and X back into shared memory; warp 8 allocates TMEM and one of its threads
-// issues the MMAs. Every mbarrier wait is bounded (about one second); on expiry the
+// Sixteen warps, four per TMEM lane quarter taking 16-wide chunks of columns or rows in
+// turn, load X_0, promote accumulators, evaluate the residual and the stop rule, write
+// G into TMEM and X back into shared memory; warp 0 allocates TMEM and thread 0 issues
+// the MMAs once a barrier has published their operands. Every mbarrier wait is bounded (about one second); on expiry the
 // problem reports a timeout, the MMAs in flight drain and TMEM is freed.
 #include <cuda.h>
 #include <math.h>
@@ -36,29 +36,26 @@
 namespace polar {
 namespace {
 
-constexpr int OC_WORKER_WARPS = 8;
-constexpr int OC_WORKERS = OC_WORKER_WARPS * 32;
-constexpr int OC_THREADS = OC_WORKERS + 32;
+constexpr int OC_WARPS = 16;          // four per TMEM lane quarter
+constexpr int OC_THREADS = OC_WARPS * 32;
 constexpr uint32_t OC_TMEM_COLS = 512;
 constexpr uint32_t OC_G_COL = 256;          // first TMEM column of G's planes
 constexpr int64_t OC_MAX_M = 256, OC_MAX_N = 128;
 
-// Plane pairs (A plane, B plane) of the split product, smallest terms first; P planes
-// use the last passes_for(P) entries.
-__constant__ int kOcPassA[6] = {1, 0, 2, 0, 1, 0};
-__constant__ int kOcPassB[6] = {1, 2, 0, 1, 0, 0};
+// Plane pairs (A plane, B plane) of the split product, smallest terms first:
+// (1,1) (0,2) (2,0) (0,1) (1,0) (0,0); P planes use the last 6, 3 or 1 of them.
+__host__ __device__ constexpr uint32_t oc_pass_a(int i) { return i == 0 ? 1u : i == 2 ? 2u : i == 4 ? 1u : 0u; }
+__host__ __device__ constexpr uint32_t oc_pass_b(int i) { return i == 0 ? 1u : i == 1 ? 2u : i == 3 ? 1u : 0u; }
 
 struct OcCtl {
-  uint64_t full[2];    // MMA -> workers: accumulator ready
-  uint64_t empty[2];   // workers -> MMA: accumulator read
-  uint64_t ops;        // workers -> MMA: operands ready (X in shared memory, or G in TMEM)
+  uint64_t full[2];    // tcgen05.commit -> all warps: accumulator ready
   uint64_t drain;
   int abort;           // a bounded wait expired
   int decision;        // 0: keep iterating, 1: stop, 2: abort
   uint32_t tmem_base;
   int pad;
   float c1, c3;
-  double red[OC_WORKER_WARPS];
+  double red[OC_WARPS];
 };
 
 __host__ __device__ __forceinline__ uint32_t oc_rows(int64_t m) { return (uint32_t)((m + 15) / 16 * 16); }
@@ -72,7 +69,14 @@ __device__ __forceinline__ uint32_t oc_off(uint32_t r, uint32_t c, uint32_t ch) 
   return (c >> 6) * ch + r * 128u + ((((c & 63u) >> 3) ^ (r & 7u)) << 4) + ((c & 7u) << 1);
 }
 
-__device__ __forceinline__ void oc_sync_workers() { asm volatile("bar.sync 1, %0;" ::"n"(OC_WORKERS) : "memory"); }
+__device__ __forceinline__ void oc_sync_workers() { asm volatile("bar.sync 1, %0;" ::"n"(OC_THREADS) : "memory"); }
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane (completed by tmem_st_wait).
+__device__ __forceinline__ void oc_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 
 __device__ __forceinline__ void oc_fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -83,132 +87,195 @@ __device__ __forceinline__ uint32_t oc_idesc(bool a_mn, bool b_mn, uint32_t n) {
 }
 
 struct OcBars {
-  uint32_t full, empty, ops, drain;
+  uint32_t full, drain;
 };
 
-template <int P>
-__device__ __noinline__ void oc_mma(uint32_t xbase, uint32_t ch, uint32_t mp, uint32_t np, uint32_t tmem, OcBars br,
-                                    volatile OcCtl* ctl, int withhold) {
-  volatile int* abort_flag = &ctl->abort;
-  constexpr int NPASS = P == 3 ? 6 : (P == 2 ? 3 : 1);
-  constexpr int P0 = 6 - NPASS;
-  const uint32_t idesc_g = oc_idesc(true, true, np);
-  const uint32_t idesc_u = oc_idesc(false, false, mp);
-  const uint32_t ks_g = mp / 16, ks_u = np / 16;
-  uint32_t ph_ops = 0, use0 = 0, use1 = 0;
-  bool issued = false;
-  while (true) {
-    // X_k is in shared memory
-    if (!mbar_wait(br.ops, ph_ops, abort_flag)) break;
-    ph_ops ^= 1u;
-    if (ctl->decision != 0) break;
-    tc_fence_after();
-    bool ok = true;
-    for (uint32_t s = 0; 4 * s < ks_g; ++s) {
-      const uint32_t b = s & 1u;
-      if (!mbar_wait(br.empty + 8 * b, ((b ? use1 : use0) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
-      tc_fence_after();
-      const uint32_t k_end = 4 * s + 4 < ks_g ? 4 * s + 4 : ks_g;
-      if (!withhold) {
-        for (int ps = 0; ps < NPASS; ++ps) {
-          const uint32_t qa = (uint32_t)kOcPassA[P0 + ps], qb = (uint32_t)kOcPassB[P0 + ps];
-          for (uint32_t kk = 4 * s; kk < k_end; ++kk) {
-            const uint64_t ad = smem_desc(xbase + 2 * qa * ch + kk * 2048, ch, 1024, 2);
-            const uint64_t bd = smem_desc(xbase + 2 * qb * ch + kk * 2048, ch, 1024, 2);
-            tc_mma(tmem + 128 * b, ad, bd, idesc_g, (ps == 0 && kk == 4 * s) ? 0u : 1u);
-          }
-        }
-        tc_commit(br.full + 8 * b);
-        issued = true;
-      }
-      if (b) ++use1; else ++use0;
-    }
-    if (!ok) break;
-    // G is in TMEM (or the workers stopped)
-    if (!mbar_wait(br.ops, ph_ops, abort_flag)) break;
-    ph_ops ^= 1u;
-    if (ctl->decision != 0) break;
-    tc_fence_after();
-    if (!mbar_wait(br.empty, (use0 & 1u) ^ 1u, abort_flag) || !mbar_wait(br.empty + 8, (use1 & 1u) ^ 1u, abort_flag))
-      break;
-    tc_fence_after();
-    if (!withhold) {
-      for (int ps = 0; ps < NPASS; ++ps) {
-        const uint32_t qa = (uint32_t)kOcPassA[P0 + ps], qb = (uint32_t)kOcPassB[P0 + ps];
-        for (uint32_t kk = 0; kk < ks_u; ++kk) {
-          const uint32_t at = tmem + OC_G_COL + 64 * qa + 8 * kk;
-          const uint64_t bd = smem_desc(xbase + (2 * qb + (kk >> 2)) * ch + (kk & 3u) * 32, 16, 1024, 2);
-          tc_mma_ts(tmem, at, bd, idesc_u, (ps == 0 && kk == 0) ? 0u : 1u);
-        }
-      }
-      tc_commit(br.full);
-      tc_commit(br.full + 8);
-      issued = true;
-    }
-    ++use0;
-    ++use1;
-  }
-  // every MMA issued has completed before the CTA frees TMEM
-  if (issued) {
-    tc_commit(br.drain);
-    mbar_drain(br.drain, 0);
+// TMEM loads without the wait, and the wait tied to the loaded registers so that no use
+// is scheduled before it (tcgen05.wait::ld covers every earlier load of the thread).
+__device__ __forceinline__ void oc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void oc_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+// Two floats to BF16 with round-to-nearest-even: lo in the low half, hi in the high half.
+__device__ __forceinline__ uint32_t oc_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ float oc_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float oc_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// The three-plane split of a pair (each value the sum of its planes exactly): planes of
+// x0 in the low halves of w[0..2], of x1 in the high halves.
+__device__ __forceinline__ void oc_split2(float x0, float x1, uint32_t (&w)[3]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    w[q] = oc_bf16x2(x0, x1);
+    x0 -= oc_lo(w[q]);
+    x1 -= oc_hi(w[q]);
   }
 }
 
+// MMA issue, by one thread: the Gram's 64-row slice s of X into accumulator s % 2, and the
+// update P^T = G X^T into columns 0 .. mp, each completed on its full barrier. Plane q of
+// X is read through MN-major descriptors (chunk stride ch, 8-row groups of 1024 bytes)
+// and K-major ones (rows of 128 bytes), built per MMA from the plane's address.
 template <int P>
-__device__ __noinline__ void oc_workers(const OcTask& tk, uint8_t* xs, uint32_t ch, uint32_t mp, uint32_t np,
-                                        uint32_t tmem, OcBars br, volatile OcCtl* ctl, const StopRule& rule,
-                                        double tol, int warp, int lane) {
+struct OcIssuer {
+  static constexpr int NPASS = P == 3 ? 6 : (P == 2 ? 3 : 1);
+  static constexpr int P0 = 6 - NPASS;
+  // descriptor high word: stride between 8-row groups 1024 bytes, version 1, 128-byte swizzle
+  static constexpr uint32_t HI = (1024u >> 4) | (1u << 14) | (2u << 29);
+  uint32_t xbase, ch, tmem, full, idesc_g, idesc_u, ks_g, ks_u;
+
+  __device__ __forceinline__ void init(uint32_t xbase_, uint32_t ch_, uint32_t mp, uint32_t np, uint32_t tmem_,
+                                       uint32_t full_) {
+    xbase = xbase_;
+    ch = ch_;
+    tmem = tmem_;
+    full = full_;
+    idesc_g = oc_idesc(true, true, np);
+    idesc_u = oc_idesc(false, false, mp);
+    ks_g = mp / 16;
+    ks_u = np / 16;
+  }
+
+  __device__ __forceinline__ static uint64_t desc(uint32_t addr, uint32_t lbo) {
+    return ((uint64_t)HI << 32) | ((addr >> 4) & 0x3FFFu) | (((lbo >> 4) & 0x3FFFu) << 16);
+  }
+
+  __device__ __forceinline__ void gram_slice(uint32_t s) {
+    const uint32_t b = s & 1u;
+    const uint32_t k_end = 4 * s + 4 < ks_g ? 4 * s + 4 : ks_g;
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps) {
+      const uint32_t a0 = xbase + 2 * oc_pass_a(P0 + ps) * ch, b0 = xbase + 2 * oc_pass_b(P0 + ps) * ch;
+      for (uint32_t kk = 4 * s; kk < k_end; ++kk)   // 16 rows of X: 2048 bytes
+        tc_mma(tmem + 128 * b, desc(a0 + kk * 2048, ch), desc(b0 + kk * 2048, ch), idesc_g,
+               (ps == 0 && kk == 4 * s) ? 0u : 1u);
+    }
+    tc_commit(full + 8 * b);
+  }
+
+  __device__ __forceinline__ void update() {
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps) {
+      const uint32_t b0 = xbase + 2 * oc_pass_b(P0 + ps) * ch;
+      for (uint32_t kk = 0; kk < ks_u; ++kk)   // 16 columns of X: 32 bytes within its 64-column chunk
+        tc_mma_ts(tmem, tmem + OC_G_COL + 64 * oc_pass_a(P0 + ps) + 8 * kk, desc(b0 + (kk >> 2) * ch + (kk & 3u) * 32, 16),
+                  idesc_u, (ps == 0 && kk == 0) ? 0u : 1u);
+    }
+    tc_commit(full);
+    tc_commit(full + 8);
+  }
+};
+
+// The whole loop for one problem, all warps. The four warps of a TMEM lane quarter take
+// 16-wide chunks in turn: chunk c of the Gram's columns and of the update's rows belongs
+// to warp sub = c % 4 of the quarter. Thread 0 issues the MMAs as soon as a barrier has
+// published their operands (X_k in shared memory, G in TMEM, an accumulator read).
+template <int P>
+__device__ __noinline__ void oc_solve(const OcTask& tk, uint8_t* xs, uint32_t xbase, uint32_t ch, uint32_t mp,
+                                      uint32_t np, uint32_t tmem, OcBars br, volatile OcCtl* ctl,
+                                      const StopRule& rule, double tol, int warp, int lane, int withhold) {
   const int tid = warp * 32 + lane;
-  const int h = warp >> 2;                            // half of the columns this warp reads
-  const uint32_t i = (uint32_t)((warp & 3) * 32 + lane);   // TMEM lane: a row of G, a column of X
+  const uint32_t sub = (uint32_t)warp >> 2;
+  const uint32_t i = (uint32_t)((warp & 3) * 32 + lane);           // TMEM lane: a row of G, a column of X
   const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
   const int64_t m = tk.m, n = tk.n;
   DevState* st = tk.st;
   volatile int* abort_flag = &ctl->abort;
-  uint32_t use0 = 0, use1 = 0;
+  // byte offset of column i in a plane for each of the 8 row phases of the swizzle
+  uint32_t colo[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) colo[e] = (i >> 6) * ch + ((((i & 63u) >> 3) ^ (uint32_t)e) << 4) + ((i & 7u) << 1);
+  OcIssuer<P> iss;
+  const bool issuer = tid == 0 && !withhold;
+  if (issuer) iss.init(xbase, ch, mp, np, tmem, br.full);
+  bool issued = false;
+  const double inv_sqrt_n = tid == 0 ? st->inv_sqrt_n : 0.0;
+  double r_km1 = 0.0, r_km2 = 0.0;                                 // thread 0: residuals of steps k-1, k-2
+  uint32_t use0 = 0, use1 = 0;                                     // completions awaited on full[0], full[1]
   const uint32_t nslices = (mp / 16 + 3) / 4;
+  const uint32_t gch = np / 16, uch = mp / 16;                     // 16-wide chunks of G's columns, X's rows
   int k = 0;
   for (;; ++k) {
-    // X_k complete in shared memory: hand it to the tensor cores
+    // X_k complete in shared memory (and the last accumulator read): the first two Gram slices
     oc_fence_async();
+    tc_fence_before();
     oc_sync_workers();
-    if (tid == 0) mbar_arrive(br.ops);
-    // ---- Gram: promote its slices
-    float g[64];
+    if (issuer && !*abort_flag) {
+      tc_fence_after();
+      iss.gram_slice(0);
+      if (nslices > 1) iss.gram_slice(1);
+      issued = true;
+    }
+    // ---- Gram: promote this warp's chunks (at most two) of every slice
+    float g[2][16];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) g[j] = 0.0f;
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) g[t][e] = 0.0f;
     for (uint32_t s = 0; s < nslices; ++s) {
       const uint32_t b = s & 1u;
       bool ok = !*abort_flag && mbar_wait(br.full + 8 * b, (b ? use1 : use0) & 1u, abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
         tc_fence_after();
-        if (64u * h < np) {
+        uint32_t v[2][16];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tmem_ld16(tmem + lane_addr + 128u * b + 64u * h + 16u * c, v);
-            add16_packed(&g[16 * c], v);
+        for (int t = 0; t < 2; ++t)
+          if (sub + 4 * t < gch) oc_ld16(tmem + lane_addr + 128u * b + 16u * (sub + 4 * t), v[t]);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (sub + 4 * t < gch) {
+            oc_wait16(v[t]);
+            float f[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[t][e]);
+            add16_packed(g[t], f);
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(br.empty + 8 * b);
       if (b) ++use1; else ++use0;
-    }
-    // ---- residual ||G - I||_F^2 over the n x n block, fixed-order reduction
-    double part = 0.0;
-#pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      const int64_t jj = 64 * h + j;
-      if (jj >= n) g[j] = 0.0f;   // columns beyond n (stale accumulator columns)
-      if ((int64_t)i < n && jj < n) {
-        const double d = (double)g[j] - ((int64_t)i == jj ? 1.0 : 0.0);
-        part = fma(d, d, part);
+      if (s + 2 < nslices) {
+        // every warp has read slice s: its accumulator takes slice s + 2
+        tc_fence_before();
+        oc_sync_workers();
+        if (issuer && !*abort_flag) {
+          tc_fence_after();
+          iss.gram_slice(s + 2);
+        }
       }
     }
+    // ---- residual ||G - I||_F^2 over the n x n block: float per thread (at most 32 terms;
+    // FP64 is slow on this part), float64 across threads in a fixed order
+    float part32 = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int64_t jj = 16 * (sub + 4 * t) + e;
+        if (jj >= n) g[t][e] = 0.0f;   // columns beyond n
+        if ((int64_t)i < n && jj < n) {
+          const float d = g[t][e] - ((int64_t)i == jj ? 1.0f : 0.0f);
+          part32 = fmaf(d, d, part32);
+        }
+      }
+    }
+    double part = (double)part32;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
     if (lane == 0) ctl->red[warp] = part;
@@ -217,91 +284,111 @@ __device__ __noinline__ void oc_workers(const OcTask& tk, uint8_t* xs, uint32_t 
       int dec = 2;
       if (!*abort_flag) {
         double sum = 0.0;
-        for (int w = 0; w < OC_WORKER_WARPS; ++w) sum += ctl->red[w];
-        const double r = sqrt(sum) * st->inv_sqrt_n;
-        const bool running = batched_step_rule(*st, rule, tol, r, k, P);
-        ctl->c1 = st->upd_c1;
-        ctl->c3 = st->upd_c3;
+        for (int w = 0; w < OC_WARPS; ++w) sum += ctl->red[w];
+        const double r = sqrt(sum) * inv_sqrt_n;
+        float c1 = 1.5f, c3 = -0.5f;
+        const bool running = batched_step_rule(*st, rule, tol, r, k >= 2 ? r_km2 : 0.0, k, P, c1, c3);
+        r_km2 = r_km1;
+        r_km1 = r;
+        ctl->c1 = c1;
+        ctl->c3 = c3;
         dec = running ? 0 : 1;
       }
       ctl->decision = dec;
     }
     oc_sync_workers();
-    const int dec = ctl->decision;
-    if (dec != 0) {
-      if (tid == 0) mbar_arrive(br.ops);   // lets the MMA thread see the decision
-      break;
-    }
+    if (ctl->decision != 0) break;
     // ---- G's planes into TMEM as the update's A operand (two BF16 per column, low half first)
-    if (64u * h < np) {
+    bool stored = false;
 #pragma unroll
-      for (int qp = 0; qp < P; ++qp) {
-        uint32_t w[32];
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t c = sub + 4 * t;
+      if (c < gch) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const uint16_t b0 = bf16_rne_bits_dev(g[2 * j]), b1 = bf16_rne_bits_dev(g[2 * j + 1]);
-          g[2 * j] -= bf16_to_f32_dev(b0);
-          g[2 * j + 1] -= bf16_to_f32_dev(b1);
-          w[j] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+        for (int qp = 0; qp < P; ++qp) {
+          uint32_t w[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            w[j] = oc_bf16x2(g[t][2 * j], g[t][2 * j + 1]);
+            g[t][2 * j] -= oc_lo(w[j]);
+            g[t][2 * j + 1] -= oc_hi(w[j]);
+          }
+          oc_st8(tmem + lane_addr + OC_G_COL + 64u * qp + 8u * c, w);
         }
-        tmem_st32(tmem + lane_addr + OC_G_COL + 64u * qp + 32u * h, w);
+        stored = true;
       }
-      tmem_st_wait();
     }
+    if (stored) tmem_st_wait();
     tc_fence_before();
     oc_sync_workers();
-    if (tid == 0) mbar_arrive(br.ops);
-    // ---- update: P^T = G X^T, then X_{k+1} = c1 X_k + c3 P in place
+    if (issuer && !*abort_flag) {
+      tc_fence_after();
+      iss.update();
+    }
+    // ---- update: P^T = G X^T, then X_{k+1} = c1 X_k + c3 P in place, this warp's 16-row
+    // chunks one at a time from TMEM with the next in flight
     bool ok = !*abort_flag && mbar_wait(br.full, use0 & 1u, abort_flag) && mbar_wait(br.full + 8, use1 & 1u, abort_flag);
     ok = __all_sync(0xffffffffu, ok);
-    float acc[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
-    if (ok) {
-      tc_fence_after();
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (128u * h + 16u * c < mp) {
-          float v[16];
-          tmem_ld16(tmem + lane_addr + 128u * h + 16u * c, v);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) acc[16 * c + e] = v[e];
-        }
-      }
-    }
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(br.empty);
-      mbar_arrive(br.empty + 8);
-    }
     ++use0;
     ++use1;
-    if (ok && (int64_t)i < n) {
+    if (ok && sub < uch) {
+      tc_fence_after();
       const float c1 = ctl->c1, c3 = ctl->c3;
+      const bool active = (int64_t)i < n;
+      uint32_t cur[16], nxt[16];
+      oc_ld16(tmem + lane_addr + 16u * sub, cur);
+      oc_wait16(cur);
+      for (uint32_t c = sub; c < uch; c += 4) {
+        const bool more = c + 4 < uch;
+        if (more) oc_ld16(tmem + lane_addr + 16u * (c + 4), nxt);
+        const uint32_t rb = 16u * c;
+        if (active && rb < (uint32_t)m) {
+          uint8_t* row = xs + rb * 128u;
 #pragma unroll
-      for (int rr = 0; rr < 128; ++rr) {
-        const int64_t r = 128 * h + rr;
-        if (r < m) {
-          const uint32_t o = oc_off((uint32_t)r, i, ch);
-          uint16_t* p0 = reinterpret_cast<uint16_t*>(xs + o);
-          uint16_t* p1 = reinterpret_cast<uint16_t*>(xs + 2 * ch + o);
-          uint16_t* p2 = reinterpret_cast<uint16_t*>(xs + 4 * ch + o);
-          const float x = (bf16_to_f32_dev(*p0) + bf16_to_f32_dev(*p1)) + bf16_to_f32_dev(*p2);
-          const float xn = c1 * x + c3 * acc[rr];
-          uint16_t qv[3];
-          split_planes_dev<3>(xn, qv);
-          *p0 = qv[0];
-          *p1 = qv[1];
-          *p2 = qv[2];
+          for (int e = 0; e < 16; e += 2) {
+            uint8_t* a0 = row + e * 128 + colo[e & 7];
+            uint8_t* a1 = row + (e + 1) * 128 + colo[(e + 1) & 7];
+            const bool v0 = rb + e < (uint32_t)m, v1 = rb + e + 1 < (uint32_t)m;
+            float x0 = 0.0f, x1 = 0.0f;
+            if (v0)
+              x0 = (bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a0)) +
+                    bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a0 + 2 * ch))) +
+                   bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a0 + 4 * ch));
+            if (v1)
+              x1 = (bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a1)) +
+                    bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a1 + 2 * ch))) +
+                   bf16_to_f32_dev(*reinterpret_cast<uint16_t*>(a1 + 4 * ch));
+            const float xn0 = c1 * x0 + c3 * __uint_as_float(cur[e]);
+            const float xn1 = c1 * x1 + c3 * __uint_as_float(cur[e + 1]);
+            uint32_t w[3];
+            oc_split2(xn0, xn1, w);
+            if (v0) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) *reinterpret_cast<uint16_t*>(a0 + 2 * q * ch) = (uint16_t)w[q];
+            }
+            if (v1) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) *reinterpret_cast<uint16_t*>(a1 + 2 * q * ch) = (uint16_t)(w[q] >> 16);
+            }
+          }
+        }
+        if (more) {
+          oc_wait16(nxt);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
         }
       }
     }
   }
+  // everything issued has completed before the CTA frees TMEM
+  if (tid == 0 && issued) {
+    tc_commit(br.drain);
+    mbar_drain(br.drain, 0);
+  }
   if (ctl->decision != 1) return;
   // ---- the final iterate's planes to global memory, where the H product and U read them
   uint16_t* dst = tk.xp[k & 1];
-  for (uint32_t u = (uint32_t)tid; u < 3u * (uint32_t)m * 16u; u += OC_WORKERS) {
+  for (uint32_t u = (uint32_t)tid; u < 3u * (uint32_t)m * 16u; u += OC_THREADS) {
     const uint32_t q = u / ((uint32_t)m * 16u), rem = u % ((uint32_t)m * 16u), r = rem >> 4, c8 = (rem & 15u) * 8u;
     if (c8 >= n) continue;
     const uint4 v = *reinterpret_cast<const uint4*>(xs + 2 * q * ch + oc_off(r, c8, ch));
@@ -331,31 +418,27 @@ __global__ void __launch_bounds__(OC_THREADS, 1)
   volatile OcCtl* ctl = reinterpret_cast<volatile OcCtl*>(xs + 6 * ch);
   OcBars br;
   br.full = smem_u32((const void*)&ctl->full[0]);
-  br.empty = smem_u32((const void*)&ctl->empty[0]);
-  br.ops = smem_u32((const void*)&ctl->ops);
   br.drain = smem_u32((const void*)&ctl->drain);
   if (threadIdx.x == 0) {
     mbar_init(br.full, 1);
     mbar_init(br.full + 8, 1);
-    mbar_init(br.empty, OC_WORKER_WARPS);
-    mbar_init(br.empty + 8, OC_WORKER_WARPS);
-    mbar_init(br.ops, 1);
     mbar_init(br.drain, 1);
     ctl->abort = 0;
     ctl->decision = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     oc_fence_async();
   }
-  if (warp == OC_WORKER_WARPS) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void*)&ctl->tmem_base)),
                  "n"(OC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  } else {
-    // X_0's three planes into shared memory, zero beyond m x n
+  }
+  // X_0's three planes into shared memory, zero beyond m x n
+  {
     const int64_t m = tk.m, n = tk.n;
-    for (uint32_t u = threadIdx.x; u < 3u * mp * 16u; u += OC_WORKERS) {
+    for (uint32_t u = threadIdx.x; u < 3u * mp * 16u; u += OC_THREADS) {
       const uint32_t q = u / (mp * 16u), rem = u % (mp * 16u), r = rem >> 4, c8 = (rem & 15u) * 8u;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (r < m && c8 < n) {
@@ -374,12 +457,8 @@ __global__ void __launch_bounds__(OC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
-  if (warp == OC_WORKER_WARPS) {
-    if (lane == 0) oc_mma<P>(xbase, ch, mp, np, tmem, br, ctl, withhold);
-  } else {
-    const double tol = (tol_dev && *tol_dev > 0) ? *tol_dev : rule.tol;
-    oc_workers<P>(tk, xs, ch, mp, np, tmem, br, ctl, rule, tol, warp, lane);
-  }
+  const double tol = (tol_dev && *tol_dev > 0) ? *tol_dev : rule.tol;
+  oc_solve<P>(tk, xs, xbase, ch, mp, np, tmem, br, ctl, rule, tol, warp, lane, withhold);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && ctl->decision == 2) {
@@ -387,7 +466,7 @@ __global__ void __launch_bounds__(OC_THREADS, 1)
     tk.st->status = ST_TIMEOUT;
     if (err_word) atomicOr(err_word, 1);
   }
-  if (warp == OC_WORKER_WARPS) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(OC_TMEM_COLS) : "memory");
   }
