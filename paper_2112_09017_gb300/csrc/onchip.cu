@@ -30,7 +30,6 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
-#include "stop_rule.cuh"
 #include "tc_ptx.cuh"
 
 namespace polar {
@@ -47,11 +46,23 @@ constexpr int64_t OC_MAX_M = 256, OC_MAX_N = 128;
 __host__ __device__ constexpr uint32_t oc_pass_a(int i) { return i == 0 ? 1u : i == 2 ? 2u : i == 4 ? 1u : 0u; }
 __host__ __device__ constexpr uint32_t oc_pass_b(int i) { return i == 0 ? 1u : i == 1 ? 2u : i == 3 ? 1u : 0u; }
 
+// The stop rule of the batched finalize on squares: with v = ||G - I||_F^2 = n r^2,
+// r <= tol is v <= n tol^2 and r > s r_{k-2} is v > s^2 v_{k-2} (one FP64 compare each
+// instead of a square root on the critical path).
+struct OcRule {
+  double v_tol, stag2, v_floor;
+  int n_pre, max_iter;
+  float pre_c1, pre_c3;
+};
+
 struct OcCtl {
   uint64_t full[2];    // tcgen05.commit -> all warps: accumulator ready
   uint64_t drain;
   int abort;           // a bounded wait expired
   int decision;        // 0: keep iterating, 1: stop, 2: abort
+  int status;          // the problem's status after the step
+  double v;            // ||G - I||_F^2 of the step
+  OcRule dr;
   uint32_t tmem_base;
   int pad;
   float c1, c3;
@@ -189,7 +200,7 @@ struct OcIssuer {
 template <int P>
 __device__ __noinline__ void oc_solve(const OcTask& tk, uint8_t* xs, uint32_t xbase, uint32_t ch, uint32_t mp,
                                       uint32_t np, uint32_t tmem, OcBars br, volatile OcCtl* ctl,
-                                      const StopRule& rule, double tol, int warp, int lane, int withhold) {
+                                      int warp, int lane, int withhold) {
   const int tid = warp * 32 + lane;
   const uint32_t sub = (uint32_t)warp >> 2;
   const uint32_t i = (uint32_t)((warp & 3) * 32 + lane);           // TMEM lane: a row of G, a column of X
@@ -205,8 +216,8 @@ __device__ __noinline__ void oc_solve(const OcTask& tk, uint8_t* xs, uint32_t xb
   const bool issuer = tid == 0 && !withhold;
   if (issuer) iss.init(xbase, ch, mp, np, tmem, br.full);
   bool issued = false;
-  const double inv_sqrt_n = tid == 0 ? st->inv_sqrt_n : 0.0;
-  double r_km1 = 0.0, r_km2 = 0.0;                                 // thread 0: residuals of steps k-1, k-2
+  const double inv_sqrt_n = tid == 32 ? st->inv_sqrt_n : 0.0;
+  double v_km1 = 0.0, v_km2 = 0.0;                                 // thread 0: sums of squares of steps k-1, k-2
   uint32_t use0 = 0, use1 = 0;                                     // completions awaited on full[0], full[1]
   const uint32_t nslices = (mp / 16 + 3) / 4;
   const uint32_t gch = np / 16, uch = mp / 16;                     // 16-wide chunks of G's columns, X's rows
@@ -260,50 +271,24 @@ __device__ __noinline__ void oc_solve(const OcTask& tk, uint8_t* xs, uint32_t xb
         }
       }
     }
-    // ---- residual ||G - I||_F^2 over the n x n block: float per thread (at most 32 terms;
-    // FP64 is slow on this part), float64 across threads in a fixed order
+    // ---- residual ||G - I||_F^2 over the n x n block (float per thread, at most 32 terms;
+    // FP64 is slow on this part), and G's planes into TMEM as the update's A operand (two
+    // BF16 per column, low half first) whatever the decision
     float part32 = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int64_t jj = 16 * (sub + 4 * t) + e;
-        if (jj >= n) g[t][e] = 0.0f;   // columns beyond n
-        if ((int64_t)i < n && jj < n) {
-          const float d = g[t][e] - ((int64_t)i == jj ? 1.0f : 0.0f);
-          part32 = fmaf(d, d, part32);
-        }
-      }
-    }
-    double part = (double)part32;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if (lane == 0) ctl->red[warp] = part;
-    oc_sync_workers();
-    if (tid == 0) {
-      int dec = 2;
-      if (!*abort_flag) {
-        double sum = 0.0;
-        for (int w = 0; w < OC_WARPS; ++w) sum += ctl->red[w];
-        const double r = sqrt(sum) * inv_sqrt_n;
-        float c1 = 1.5f, c3 = -0.5f;
-        const bool running = batched_step_rule(*st, rule, tol, r, k >= 2 ? r_km2 : 0.0, k, P, c1, c3);
-        r_km2 = r_km1;
-        r_km1 = r;
-        ctl->c1 = c1;
-        ctl->c3 = c3;
-        dec = running ? 0 : 1;
-      }
-      ctl->decision = dec;
-    }
-    oc_sync_workers();
-    if (ctl->decision != 0) break;
-    // ---- G's planes into TMEM as the update's A operand (two BF16 per column, low half first)
     bool stored = false;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const uint32_t c = sub + 4 * t;
       if (c < gch) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int64_t jj = 16 * c + e;
+          if (jj >= n) g[t][e] = 0.0f;   // columns beyond n
+          if ((int64_t)i < n && jj < n) {
+            const float d = g[t][e] - ((int64_t)i == jj ? 1.0f : 0.0f);
+            part32 = fmaf(d, d, part32);
+          }
+        }
 #pragma unroll
         for (int qp = 0; qp < P; ++qp) {
           uint32_t w[8];
@@ -319,12 +304,61 @@ __device__ __noinline__ void oc_solve(const OcTask& tk, uint8_t* xs, uint32_t xb
       }
     }
     if (stored) tmem_st_wait();
+    double part = (double)part32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if (lane == 0) ctl->red[warp] = part;
     tc_fence_before();
     oc_sync_workers();
-    if (issuer && !*abort_flag) {
-      tc_fence_after();
-      iss.update();
+    // ---- the stop rule: warp 0 sums the warps' partials in a fixed order and thread 0
+    // decides on the sum of squares v = n r^2 against squared thresholds, then issues the
+    // update at once; thread 32 records r and the outcome while the update runs
+    if (warp == 0) {
+      double v = lane < OC_WARPS ? ctl->red[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        int dec = 2, status = ST_TIMEOUT;
+        if (!*abort_flag) {
+          const bool testing = k >= ctl->dr.n_pre;
+          if (!isfinite(v)) status = ST_NONFINITE;
+          else if (testing && v <= ctl->dr.v_tol) status = ST_CONVERGED;
+          else if (testing && k >= ctl->dr.n_pre + 2 && v > ctl->dr.stag2 * v_km2 && v < ctl->dr.v_floor) status = ST_NOT_CONVERGED;
+          else if (k >= ctl->dr.max_iter) status = ST_NOT_CONVERGED;
+          else status = ST_RUNNING;
+          dec = status == ST_RUNNING ? 0 : 1;
+          ctl->c1 = k < ctl->dr.n_pre ? ctl->dr.pre_c1 : 1.5f;
+          ctl->c3 = k < ctl->dr.n_pre ? ctl->dr.pre_c3 : -0.5f;
+          ctl->status = status;
+          ctl->v = v;
+        }
+        ctl->decision = dec;
+        v_km2 = v_km1;
+        v_km1 = v;
+        if (dec == 0 && issuer) {
+          tc_fence_after();
+          iss.update();
+        }
+      }
     }
+    oc_sync_workers();
+    if (tid == 32 && ctl->decision != 2) {
+      // the record of step k, as the batched finalize keeps it
+      const double r = sqrt(ctl->v) * inv_sqrt_n;
+      if (k < POLAR_HIST) {
+        st->res_hist[k] = r;
+        st->planes_hist[k] = (unsigned char)P;
+        st->hist_len = k + 1;
+      }
+      st->ring[k & 3] = r;
+      st->iters = k;
+      if (ctl->status != ST_RUNNING) st->status = ctl->status;
+      else {
+        st->upd_c1 = ctl->c1;
+        st->upd_c3 = ctl->c3;
+      }
+    }
+    if (ctl->decision != 0) break;
     // ---- update: P^T = G X^T, then X_{k+1} = c1 X_k + c3 P in place, this warp's 16-row
     // chunks one at a time from TMEM with the next in flight
     bool ok = !*abort_flag && mbar_wait(br.full, use0 & 1u, abort_flag) && mbar_wait(br.full + 8, use1 & 1u, abort_flag);
@@ -425,6 +459,15 @@ __global__ void __launch_bounds__(OC_THREADS, 1)
     mbar_init(br.drain, 1);
     ctl->abort = 0;
     ctl->decision = 0;
+    const double tol = (tol_dev && *tol_dev > 0) ? *tol_dev : rule.tol;
+    const double nn = (double)tk.n;
+    ctl->dr.v_tol = tol * tol * nn;
+    ctl->dr.stag2 = rule.stagnation * rule.stagnation;
+    ctl->dr.v_floor = rule.stag_floor * rule.stag_floor * nn;
+    ctl->dr.n_pre = rule.n_pre;
+    ctl->dr.max_iter = rule.max_iter;
+    ctl->dr.pre_c1 = (float)rule.pre_a;
+    ctl->dr.pre_c3 = (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     oc_fence_async();
   }
@@ -457,8 +500,7 @@ __global__ void __launch_bounds__(OC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
-  const double tol = (tol_dev && *tol_dev > 0) ? *tol_dev : rule.tol;
-  oc_solve<P>(tk, xs, xbase, ch, mp, np, tmem, br, ctl, rule, tol, warp, lane, withhold);
+  oc_solve<P>(tk, xs, xbase, ch, mp, np, tmem, br, ctl, warp, lane, withhold);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && ctl->decision == 2) {
