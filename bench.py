@@ -11,7 +11,8 @@ matrix with a prescribed spectrum, input resident in HBM.
 
 Beside the headline solve the line carries measured legs on the same shape: the plain FP32
 form, the preconditioned iteration (Algorithm 1), the Newton-Schulz inverse (Algorithm 2),
-a Chebyshev matrix function by Clenshaw summation, and the batched configuration.
+a Chebyshev matrix function by Clenshaw summation, the batched configuration, and a batch of
+small problems (n on [64, 128]) solved one SM each, timed against the grouped tile path.
 
 Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
 problem of the same size (independent replicas; the single solve does not shard),
@@ -46,7 +47,7 @@ def kernel_source_hash():
     """First 16 hex digits of sha256 over the tensor-core kernel's sources."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("gemm_tc.cu", "internal.cuh", "device_util.cuh"):
+    for f in ("gemm_tc.cu", "internal.cuh", "device_util.cuh", "tc_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_2112_09017_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -204,12 +205,14 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def run_batched(lib, torch, count, steps, warmup):
-    """The batched workload: `count` problems (n uniform on [64, 1024], m = n or 2n,
-    sigma on [1e-3, 1]) in one polar_batched_run; solves/s and per-problem iterations."""
+def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, As=None):
+    """The batched workload: `count` problems (n uniform on [n_lo, n_hi], m = n or 2n,
+    sigma on [1e-3, 1]) in one polar_batched_run; solves/s and per-problem iterations.
+    onchip = 0 sends the problems that fit one SM through the grouped tile kernels too."""
     from paper_2112_09017_gb300 import synth
     t0 = time.perf_counter()
-    As = [synth.batched_problem_on_device(i, "cuda") for i in range(count)]
+    if As is None:
+        As = [synth.batched_problem_on_device(i, "cuda", 1e-3, n_lo, n_hi) for i in range(count)]
     gen_s = time.perf_counter() - t0
     ms = [a.shape[0] for a in As]
     ns = [a.shape[1] for a in As]
@@ -217,6 +220,7 @@ def run_batched(lib, torch, count, steps, warmup):
     Hs = [torch.empty((n, n), dtype=torch.float32, device="cuda") for n in ns]
     o = lib.polar_default_options()
     o.prec = lib.POLAR_BF16X6
+    o.small_onchip = onchip
     t0 = time.perf_counter()
     plan = lib.polar_batched_plan_create(ms, ns, o)
     plan_s = time.perf_counter() - t0
@@ -242,7 +246,13 @@ def run_batched(lib, torch, count, steps, warmup):
         acc.append(accuracy(torch, As[i], Us[i], Hs[i]))
     lib.polar_plan_destroy(plan)
     import numpy as np
-    return {"workload": f"batched{count}_k1e3", "count": count, "ms_per_batch": ms_run,
+    # executed split-BF16 MMA work of the problems solved on one SM (M padded to 128, m and n to 16;
+    # k + 1 Grams and k updates of 2 x 128 x n x m each, six passes)
+    small = [(m, n, kk) for m, n, kk in zip(ms, ns, k) if onchip and n <= 128 and m <= 256]
+    mma_small = sum(6.0 * 2 * 128 * (-(-n // 16) * 16) * (-(-m // 16) * 16) * (2 * kk + 1) for m, n, kk in small)
+    return {"workload": f"batched{count}_n{n_lo}-{n_hi}_k1e3", "count": count, "ms_per_batch": ms_run,
+            "small_onchip": onchip, "problems_on_chip": len(small),
+            "onchip_mma_tflops": mma_small / (ms_run * 1e-3) / 1e12 if small else None,
             "solves_per_s": count / (ms_run * 1e-3), "value": flops / (ms_run * 1e-3) / 1e12, "unit": "TFLOP/s",
             "converged": int(conv.sum()), "iters_p50": float(np.percentile(k, 50)),
             "iters_p99": float(np.percentile(k, 99)), "max_residual": float(rs.max().item()),
@@ -529,6 +539,20 @@ def run_ours(args):
     if args.batched > 0:
         batched = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1)
 
+    # ---- small batched problems (n on [64, 128]): one SM each, against the grouped tile path ----
+    small = None
+    if args.batched > 0:
+        from paper_2112_09017_gb300 import synth
+        As = [synth.batched_problem_on_device(i, "cuda", 1e-3, 64, 128) for i in range(args.batched)]
+        on = run_batched(lib, torch, args.batched, max(1, min(args.steps, 3)), 2, 64, 128, onchip=1, As=As)
+        off = run_batched(lib, torch, args.batched, max(1, min(args.steps, 3)), 2, 64, 128, onchip=0, As=As)
+        peak_s = peaks.get("bf16_tflops_sustained")
+        small = {"onchip": on, "grouped": {k2: off[k2] for k2 in ("ms_per_batch", "solves_per_s", "value", "iters_p50")},
+                 "speedup_onchip_vs_grouped": off["ms_per_batch"] / on["ms_per_batch"],
+                 "onchip_tensor_frac_of_measured_sustained": (on["onchip_mma_tflops"] / peak_s)
+                 if (peak_s and on["onchip_mma_tflops"]) else None}
+        del As
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if not args.no_cpu and world == 1:
@@ -556,7 +580,7 @@ def run_ours(args):
             "plain_fp32": plain, "plain_fp32_cublas_context": cublas,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-            "batched": batched, "preconditioned": pre, "ns_inverse": inverse,
+            "batched": batched, "batched_small": small, "preconditioned": pre, "ns_inverse": inverse,
             "chebyshev": cheb,
         }
         print(json.dumps(line), flush=True)
