@@ -522,6 +522,20 @@ def run_ours(args):
                "iters": qinfos[-1]["iters"], "n_precond": qinfos[-1]["n_precond"], **qacc,
                "speedup_vs_fixed_form": (ms / args.steps) / (qms / qsteps)}
 
+    # ---- reduced-precision variants of the same solve, flagged against the 5e-6 bounds ----
+    variants = None
+    if not args.no_variants and args.prec == "bf16x6":
+        variants = {}
+        for vp in ("bf16x3", "bf16_then_x3", "bf16"):
+            vplan = lib.Plan(m, n, prec=vp, tol=w.tol)
+            vms, vinfos, _ = timed(vplan, max(1, min(args.steps, 2)), min(args.warmup, 2))
+            vacc = accuracy(torch, A, U, H)
+            vplan.close()
+            vit = vinfos[-1]["iters"]
+            variants[vp] = {"ms_per_step": vms / len(vinfos), "iters": vit,
+                            "status": "converged" if vinfos[-1]["status"] == lib.POLAR_OK else "not_converged",
+                            **vacc, "meets_5e-6": bool(vacc["orth"] <= 5e-6 and vacc["bwd"] <= 5e-6)}
+
     # ---- Algorithm 2 (Newton-Schulz inverse) on a well-conditioned matrix of the same shape ----
     inverse = None
     if not args.no_inverse:
@@ -581,7 +595,7 @@ def run_ours(args):
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "batched": batched, "batched_small": small, "preconditioned": pre, "ns_inverse": inverse,
-            "chebyshev": cheb,
+            "chebyshev": cheb, "precision_variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -604,6 +618,7 @@ def main():
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioned (Algorithm 1) leg")
     ap.add_argument("--no-inverse", action="store_true", help="skip the Newton-Schulz inverse (Algorithm 2) leg")
     ap.add_argument("--no-chebyshev", action="store_true", help="skip the Chebyshev / Clenshaw leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the reduced-precision variants")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
