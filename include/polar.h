@@ -45,7 +45,7 @@ typedef enum {
   POLAR_ECUDA = -3,         /* CUDA runtime/driver error, or no sm_103 device */
   POLAR_ENONFINITE = -4,    /* ||A||_F is zero, Inf or NaN, or a residual became non-finite */
   POLAR_ETIMEOUT = -5,      /* a bounded device-side wait expired (kernel returned early) */
-  POLAR_ENOTSUP = -6        /* precision mode or shape not supported by this build */
+  POLAR_ENOTSUP = -6        /* precision mode or shape not implemented by the library */
 } polar_status_t;
 
 /* How the matrix products of the iteration are computed.
@@ -56,7 +56,7 @@ typedef enum {
  *   BF16      1 BF16 plane, 1 pass
  *   SCHED_BF16_THEN_X3   BF16 while the residual is above switch_residual, then BF16X3
  *   AUTO      BF16X6 for n >= 256, FP32 below
- * TF32X3 and SCHED_FP8_BF16_X3 are reserved (POLAR_ENOTSUP in this build). */
+ * TF32X3 and SCHED_FP8_BF16_X3 are reserved and return POLAR_ENOTSUP. */
 typedef enum {
   POLAR_FP32 = 0,
   POLAR_BF16X6 = 1,

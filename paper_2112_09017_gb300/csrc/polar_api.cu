@@ -152,7 +152,7 @@ const char* polar_status_string(polar_status_t s) {
     case POLAR_ECUDA: return "CUDA error or no sm_103 device";
     case POLAR_ENONFINITE: return "input norm or residual is zero or non-finite";
     case POLAR_ETIMEOUT: return "a bounded device wait expired";
-    case POLAR_ENOTSUP: return "not supported by this build";
+    case POLAR_ENOTSUP: return "not supported by the library";
   }
   return "unknown status";
 }
