@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["bf16_rne_bits", "bf16_rne", "split_planes", "plane_pairs", "emulated_matmul",
-           "bits_to_float"]
+           "bits_to_float", "e4m3_rne", "quantize_tiles_e4m3", "E4M3_MAX"]
 
 PAIRS = {
     1: ((0, 0),),
@@ -83,3 +83,46 @@ def emulated_matmul(a, b, p: int) -> np.ndarray:
     for i, j in plane_pairs(p):
         acc += ap[i] @ bp[j]
     return acc
+
+
+# ---- FP8 E4M3 with per-tile power-of-two scales (the early iterations of the FP8 schedule) ----
+#
+# E4M3: 1 sign, 4 exponent (bias 7), 3 mantissa bits; no infinities; largest finite 448;
+# smallest normal 2^-6, subnormals down to 2^-9. Rounding to nearest, ties to even, and
+# saturation of finite values beyond 448 to +-448 ("satfinite").
+E4M3_MAX = 448.0
+
+
+def e4m3_rne(x) -> np.ndarray:
+    """x (float32 values) rounded to the nearest E4M3 value, ties to even, saturating."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    with np.errstate(divide="ignore"):
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    e = np.maximum(e, -6.0)                       # subnormals share the quantum of the smallest binade
+    quantum = np.exp2(e - 3.0)                    # three mantissa bits
+    q = np.rint(a / quantum) * quantum            # ties to even on the integer multiple
+    q = np.minimum(q, E4M3_MAX)
+    return (np.sign(x) * q).astype(np.float32)
+
+
+def quantize_tiles_e4m3(x, tile: int = 128) -> np.ndarray:
+    """Per tile x tile block: s = the smallest power of two with amax / s <= 448 (1 for an all-zero
+    block), and every entry replaced by s * e4m3_rne(x / s), the value an FP8 E4M3 operand with
+    that scale stands for (exact in BF16 and FP32)."""
+    x = np.asarray(x, dtype=np.float32)
+    out = np.empty_like(x)
+    rows, cols = x.shape
+    for i in range(0, rows, tile):
+        for j in range(0, cols, tile):
+            b = x[i:i + tile, j:j + tile].astype(np.float64)
+            amax = float(np.max(np.abs(b))) if b.size else 0.0
+            s = 1.0
+            if amax > 0:
+                s = 2.0 ** int(np.ceil(np.log2(amax / E4M3_MAX)))
+                while amax / s > E4M3_MAX:            # guard against log2 rounding
+                    s *= 2.0
+                while s > 0 and amax / (s / 2.0) <= E4M3_MAX:
+                    s /= 2.0
+            out[i:i + tile, j:j + tile] = (e4m3_rne(b / s).astype(np.float64) * s).astype(np.float32)
+    return out
