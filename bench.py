@@ -526,7 +526,7 @@ def run_ours(args):
     variants = None
     if not args.no_variants and args.prec == "bf16x6":
         variants = {}
-        for vp in ("bf16x3", "bf16_then_x3", "bf16"):
+        for vp in ("bf16x3", "bf16_then_x3", "bf16", "fp8_bf16_x3"):
             vplan = lib.Plan(m, n, prec=vp, tol=w.tol)
             vms, vinfos, _ = timed(vplan, max(1, min(args.steps, 2)), min(args.warmup, 2))
             vacc = accuracy(torch, A, U, H)

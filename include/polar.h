@@ -55,8 +55,13 @@ typedef enum {
  *   BF16X3    2 BF16 planes, 3 passes (hi*hi, hi*lo, lo*hi)
  *   BF16      1 BF16 plane, 1 pass
  *   SCHED_BF16_THEN_X3   BF16 while the residual is above switch_residual, then BF16X3
+ *   SCHED_FP8_BF16_X3    while the residual is above fp8_switch_residual, both products take FP8 E4M3
+ *             operands with a power-of-two scale per 128 x 128 tile (computed on the BF16 tensor-core
+ *             path, where such values are exact); then as SCHED_BF16_THEN_X3 (single plans only)
  *   AUTO      BF16X6 for n >= 256, FP32 below
- * TF32X3 and SCHED_FP8_BF16_X3 are reserved and return POLAR_ENOTSUP. */
+ * The schedules do not meet the 5e-6 orthogonality / backward-error target: a product made at a
+ * precision u leaves a backward error of about u that the iteration never removes; BF16X6 (or the
+ * FP32 form) does. TF32X3 is reserved and returns POLAR_ENOTSUP. */
 typedef enum {
   POLAR_FP32 = 0,
   POLAR_BF16X6 = 1,
@@ -85,6 +90,7 @@ typedef struct {
                               s_minus under Eq. RogueScalar; then Newton-Schulz. Stop tests start after them */
   double s_minus;          /* preconditioning threshold; <= 0 means 0.1 */
   double s0;               /* estimate of the smallest singular value of A / ||A||_F; <= 0 means 2^-23 */
+  double fp8_switch_residual; /* SCHED_FP8_BF16_X3: residual below which the FP8 phase ends; <= 0 means 0.5 */
   int small_onchip;        /* batched plans with a fixed plane count: nonzero (the default) solves every
                               problem with n <= 128 and m <= 256 in one CTA that keeps X, G and the
                               accumulators on its SM for the whole loop; 0 sends them through the
@@ -213,6 +219,15 @@ POLAR_API polar_status_t polar_chebyshev_fit(const double* g, int degree, double
 POLAR_API polar_status_t polar_chebyshev(const float* A, int64_t n, int64_t lda, double a, double b,
                                          const double* coef, int degree, float* F, int64_t ldf, int prec,
                                          polar_stream_t stream);
+
+/* FP8 E4M3 quantization as the FP8 schedule applies it, for checking: each 128 x 128 tile of X
+ * (rows x cols, ldx >= cols, float32, device) is scaled by s = 2^t, the smallest power of two with
+ * max|x| <= 448 s over the tile (s = 1 for a zero tile), rounded to E4M3 with round-to-nearest-even
+ * and saturation at +-448, and scaled back: Y = s * e4m3(X / s) (float32, ldy >= cols; may equal X
+ * with ldy = ldx). Stream-asynchronous. The paper has no counterpart: its schedules are configuration
+ * choices of this library. Returns OK, EINVAL or ECUDA. */
+POLAR_API polar_status_t polar_quantize_e4m3(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
+                                             int64_t ldy, polar_stream_t stream);
 
 /* Size of the static device array behind polar_gemm_noalloc (32 MiB). */
 #define POLAR_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcArgs p, int64_t tm, int64_t tn, int64_t ntiles) {
   if (p.st && p.st->status != ST_RUNNING) return;
+  if (p.planes_dyn && *p.planes_dyn <= 0) return;   // a schedule's launch for a phase that is not current
   SingleSrc src;
   src.ma = &tmA;
   src.mb = &tmB;

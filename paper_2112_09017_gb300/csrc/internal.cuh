@@ -26,7 +26,7 @@ struct DevState {
   int planes_next;       // planes of the next product (schedules)
   int hist_len;
   unsigned int err_flags;// device error bits (timeouts)
-  int pad;
+  int fp8_on;            // FP8 schedule: 1 while the products take E4M3-quantized operands
   float upd_c1, upd_c3;  // the next update is X <- upd_c1 X + upd_c3 X G
   double ring[4];        // r_k at slot k % 4 (stagnation test beyond the history)
   double sym_err;        // ||skew(U^T A)||_F / ||U^T A||_F
@@ -41,10 +41,11 @@ struct StopRule {
   double stag_floor;
   double switch_residual;
   int max_iter;
-  int sched;      // 0: fixed planes, 1: BF16 then BF16X3
+  int sched;      // 0: fixed planes, 1: BF16 then BF16X3, 2: FP8 E4M3, then BF16, then BF16X3
   int planes_fixed;
   int n_pre;      // preconditioning steps (Algorithm 1) before the Newton-Schulz steps
   double pre_a;   // their coefficient a = 3 sqrt(3)/2 - s_minus
+  double fp8_switch;  // schedule 2: residual below which the FP8 phase ends
 };
 // Number of Eq. RogueScalar steps lifting s0 to s_minus (the first loop of Algorithm 1).
 int precond_steps(double s_minus, double s0);
@@ -69,7 +70,7 @@ int frob_partials_blocks(int64_t m, int64_t n);
 cudaError_t launch_frob_partials(const float* A, int64_t m, int64_t n, int64_t lda, double* partials,
                                  int blocks, cudaStream_t s);
 cudaError_t launch_norm_finalize(const double* partials, int nparts, DevState* st, double inv_sqrt_n,
-                                 int planes_first, cudaStream_t s);
+                                 int planes_first, int fp8_first, cudaStream_t s);
 // dst = src / ||A||_F (if scale) or src (otherwise); optional float32 copy and BF16 planes.
 cudaError_t launch_scale_split(const float* src, int64_t lds, int64_t m, int64_t n, const DevState* st,
                                bool scale, float* dst, int64_t ldd, uint16_t* planes, int64_t ldp,
@@ -99,6 +100,14 @@ cudaError_t launch_inverse_finalize(const double* partials, int npairs, DevState
 // dst = plane_0 + plane_1 + plane_2 (the FP32 value the three BF16 planes encode exactly)
 cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t plane_stride, int64_t m, int64_t n,
                                  float* dst, int64_t ldd, cudaStream_t s);
+// FP8 E4M3 with a power-of-two scale per 128 x 128 tile (the smallest s with amax / s <= 448):
+// every entry becomes s * e4m3_rne(x / s), written as one BF16 plane (exact). Source: the
+// three planes of an iterate (pitch ldp, plane stride sps); skipped unless st->fp8_on.
+cudaError_t launch_quantize_e4m3_planes(const uint16_t* src, int64_t ldp, int64_t sps, int64_t rows, int64_t cols,
+                                        uint16_t* dst, int64_t ldd, const DevState* st, cudaStream_t s);
+// The same from a float32 matrix into a float32 matrix (library service).
+cudaError_t launch_quantize_e4m3_f32(const float* src, int64_t lds, int64_t rows, int64_t cols, float* dst,
+                                     int64_t ldd, cudaStream_t s);
 // Clenshaw set-up (n x n): planes of s1 (alpha_map S + beta_map I) + s0 I, S the symmetric matrix
 // whose upper triangle is A's, each value rounded once to float32 and split into `nplanes` planes.
 cudaError_t launch_cheb_affine_split(const float* A, int64_t lda, int64_t n, double alpha_map, double beta_map,
@@ -151,7 +160,8 @@ struct TcArgs {
   DevState* st;                                   // skip when not RUNNING; error flags
   int slice_stages;                               // k-stages per promoted slice (0: library default)
   const int* planes_dyn;                          // if non-null: passes use min(*planes_dyn, nplanes)
-                                                  // planes (schedules); outputs keep out_nplanes
+                                                  // planes (schedules); outputs keep out_nplanes;
+                                                  // the launch does nothing while *planes_dyn <= 0
   int withhold_tma;                               // test hook: the producer issues no copies, so the
                                                   // bounded waits expire (set by the launcher)
 };

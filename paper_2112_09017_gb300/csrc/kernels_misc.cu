@@ -5,6 +5,7 @@
 //  - the residual finalize and stop rule ||G - I||_F / sqrt(n) <= tol;
 //  - H = (C + C^T) / 2 from C = U^T A with the symmetry check;
 //  - mirror of an upper-triangle Gram to the full symmetric matrix.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "internal.cuh"
@@ -55,7 +56,7 @@ __global__ void frob_partials_kernel(const float* __restrict__ A, int64_t m, int
 }
 
 __global__ void norm_finalize_kernel(const double* __restrict__ partials, int nparts, DevState* st,
-                                     double inv_sqrt_n, int planes_first) {
+                                     double inv_sqrt_n, int planes_first, int fp8_first) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
   double t = block_sum(acc);
@@ -66,7 +67,8 @@ __global__ void norm_finalize_kernel(const double* __restrict__ partials, int np
     st->iters = 0;
     st->hist_len = 0;
     st->err_flags = 0;
-    st->planes_next = planes_first;
+    st->planes_next = planes_first;   // 0 with fp8_first: the FP8 phase of schedule 2
+    st->fp8_on = fp8_first;
     st->sym_err = 0.0;
     st->upd_c1 = 1.5f;
     st->upd_c3 = -0.5f;
@@ -137,7 +139,12 @@ __global__ void residual_finalize_kernel(const double* __restrict__ partials, in
   } else if (k >= rule.max_iter) {
     st->status = ST_NOT_CONVERGED;
   } else {
-    st->planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
+    if (rule.sched == 2) {  // FP8 operands while r > fp8_switch (once ended, for good), then as schedule 1
+      if (st->fp8_on && !(r > rule.fp8_switch)) st->fp8_on = 0;
+      st->planes_next = st->fp8_on ? 0 : (r > rule.switch_residual ? 1 : 2);
+    } else {
+      st->planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
+    }
     if (k < rule.n_pre) {  // Eq. RogueMatrix: X <- a X - (4/27) a^3 X G
       st->upd_c1 = (float)rule.pre_a;
       st->upd_c3 = (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a);
@@ -318,6 +325,65 @@ __global__ void cheb_affine_split_kernel(const float* __restrict__ A, int64_t ld
   }
 }
 
+// FP8 E4M3 with a power-of-two scale per 128 x 128 tile. One tile per block pass: the tile's
+// amax (a block reduction), s = 2^t with t the smallest exponent such that amax <= 448 s
+// (amax = m 2^e, m in [0.5, 1): t = e - 9, or e - 8 when m > 0.875, since 448 = 0.875 2^9),
+// then s * e4m3(x / s) with round-to-nearest-even and saturation (cvt.rn.satfinite), exact
+// in BF16 and FP32. An all-zero or non-finite tile keeps s = 1.
+template <bool FROM_PLANES, bool TO_BF16>
+__global__ void quantize_e4m3_kernel(const void* __restrict__ src, int64_t lds, int64_t sps, int64_t rows,
+                                     int64_t cols, void* __restrict__ dst, int64_t ldd, const DevState* st) {
+  if (st && (st->status != ST_RUNNING || !st->fp8_on)) return;
+  __shared__ float red[kThreads / 32];
+  const int64_t tr = (rows + 127) / 128, tc = (cols + 127) / 128;
+  for (int64_t b = blockIdx.x; b < tr * tc; b += gridDim.x) {
+    const int64_t r0 = (b / tc) * 128, c0 = (b % tc) * 128;
+    float v[64];
+    float amax = 0.0f;
+#pragma unroll 8
+    for (int i = 0; i < 64; ++i) {
+      const int e = threadIdx.x + kThreads * i;   // 128 x 128 entries, 256 threads
+      const int64_t gr = r0 + (e >> 7), gc = c0 + (e & 127);
+      float x = 0.0f;
+      if (gr < rows && gc < cols) {
+        if (FROM_PLANES) {
+          const uint16_t* p = reinterpret_cast<const uint16_t*>(src) + gr * lds + gc;
+          x = (bf16_bits_to_float(p[0]) + bf16_bits_to_float(p[sps])) + bf16_bits_to_float(p[2 * sps]);
+        } else {
+          x = reinterpret_cast<const float*>(src)[gr * lds + gc];
+        }
+      }
+      v[i] = x;
+      amax = fmaxf(amax, fabsf(x));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    amax = red[0];
+    for (int w = 1; w < kThreads / 32; ++w) amax = fmaxf(amax, red[w]);
+    int t = 0;
+    if (amax > 0.0f && isfinite(amax)) {
+      int e;
+      const float m = frexpf(amax, &e);
+      t = e - 9 + (m > 0.875f ? 1 : 0);
+    }
+#pragma unroll 8
+    for (int i = 0; i < 64; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      const int64_t gr = r0 + (e >> 7), gc = c0 + (e & 127);
+      if (gr >= rows || gc >= cols) continue;
+      uint16_t q8;
+      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(q8) : "f"(0.0f), "f"(ldexpf(v[i], -t)));
+      uint32_t h2;
+      asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(q8));
+      const float q = ldexpf(__half2float(__ushort_as_half((unsigned short)(h2 & 0xffffu))), t);
+      if (TO_BF16) reinterpret_cast<uint16_t*>(dst)[gr * ldd + gc] = (uint16_t)(__float_as_uint(q) >> 16);
+      else reinterpret_cast<float*>(dst)[gr * ldd + gc] = q;
+    }
+  }
+}
+
 __global__ void inverse_init_kernel(DevState* st) {
   st->upd_c1 = 2.0f;   // X' = X (2I - A X) = 2 X - X (A X)
   st->upd_c3 = -1.0f;
@@ -376,8 +442,8 @@ cudaError_t launch_frob_partials(const float* A, int64_t m, int64_t n, int64_t l
 }
 
 cudaError_t launch_norm_finalize(const double* partials, int nparts, DevState* st, double inv_sqrt_n,
-                                 int planes_first, cudaStream_t s) {
-  norm_finalize_kernel<<<1, kThreads, 0, s>>>(partials, nparts, st, inv_sqrt_n, planes_first);
+                                 int planes_first, int fp8_first, cudaStream_t s) {
+  norm_finalize_kernel<<<1, kThreads, 0, s>>>(partials, nparts, st, inv_sqrt_n, planes_first, fp8_first);
   return cudaGetLastError();
 }
 
@@ -457,6 +523,22 @@ cudaError_t launch_cheb_affine_split(const float* A, int64_t lda, int64_t n, dou
   const int64_t tiles = ((n + 31) / 32) * ((n + 31) / 32);
   cheb_affine_split_kernel<<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(
       A, lda, n, alpha_map, beta_map, s1, s0, planes, ldp, plane_stride, nplanes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_e4m3_planes(const uint16_t* src, int64_t ldp, int64_t sps, int64_t rows, int64_t cols,
+                                        uint16_t* dst, int64_t ldd, const DevState* st, cudaStream_t s) {
+  const int64_t tiles = ((rows + 127) / 128) * ((cols + 127) / 128);
+  quantize_e4m3_kernel<true, true><<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(src, ldp, sps, rows, cols,
+                                                                                          dst, ldd, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_e4m3_f32(const float* src, int64_t lds, int64_t rows, int64_t cols, float* dst,
+                                     int64_t ldd, cudaStream_t s) {
+  const int64_t tiles = ((rows + 127) / 128) * ((cols + 127) / 128);
+  quantize_e4m3_kernel<false, false><<<(int)(tiles < 8192 ? tiles : 8192), kThreads, 0, s>>>(src, lds, 0, rows, cols,
+                                                                                            dst, ldd, nullptr);
   return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ int planes_of(int prec) {
     case POLAR_BF16X3: return 2;
     case POLAR_BF16: return 1;
     case POLAR_SCHED_BF16_THEN_X3: return 2;  // workspace for the finer phase
+    case POLAR_SCHED_FP8_BF16_X3: return 2;
     default: return 0;
   }
 }
@@ -105,6 +106,8 @@ struct polar_plan_s {
   uint16_t* Xp[2] = {nullptr, nullptr};  // BF16 planes of X (double buffer)
   uint16_t* Gp = nullptr;                // BF16 planes of G
   uint16_t* Ap = nullptr;                // BF16 planes of A (for H)
+  uint16_t* Xq = nullptr;                // FP8 schedule: E4M3-quantized X_k and G (one BF16 plane each)
+  uint16_t* Gq = nullptr;
   int64_t ldp = 0;                       // plane row pitch (elements)
   int64_t xps = 0, gps = 0;              // plane strides (elements)
   double* partials = nullptr;
@@ -141,6 +144,7 @@ void polar_default_options(polar_options_t* o) {
   o->s_minus = 0.1;
   o->s0 = 0.0;
   o->small_onchip = 1;
+  o->fp8_switch_residual = 0.5;
 }
 
 const char* polar_status_string(polar_status_t s) {
@@ -185,6 +189,7 @@ void normalize_options(polar_options_t& o) {
   if (!(o.switch_residual > 0)) o.switch_residual = 1e-2;
   if (!(o.s_minus > 0) || o.s_minus >= 1.0) o.s_minus = 0.1;
   if (!(o.s0 > 0)) o.s0 = 1.1920928955078125e-07;  // 2^-23, single-precision machine epsilon
+  if (!(o.fp8_switch_residual > 0)) o.fp8_switch_residual = 0.5;
 }
 
 int resolve_prec(int prec, int64_t n) {
@@ -258,6 +263,14 @@ polar_status_t plan_setup(polar_plan_s* p) {
     if ((r = plan_alloc(p, (size_t)p->P * p->xps * 2, &v)) != POLAR_OK) return r;
     CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));
     p->Ap = (uint16_t*)v;
+    if (p->prec == POLAR_SCHED_FP8_BF16_X3) {
+      if ((r = plan_alloc(p, (size_t)p->xps * 2, &v)) != POLAR_OK) return r;
+      CK(cudaMemset(v, 0, (size_t)p->xps * 2));
+      p->Xq = (uint16_t*)v;
+      if ((r = plan_alloc(p, (size_t)p->gps * 2, &v)) != POLAR_OK) return r;
+      CK(cudaMemset(v, 0, (size_t)p->gps * 2));
+      p->Gq = (uint16_t*)v;
+    }
   }
   if ((r = plan_alloc(p, (size_t)n * p->ldg * 4, &v)) != POLAR_OK) return r;
   p->G = (float*)v;
@@ -286,7 +299,8 @@ StopRule make_rule(const polar_plan_s* p, double tol) {
   r.stag_floor = p->opt.stag_floor;
   r.switch_residual = p->opt.switch_residual;
   r.max_iter = p->opt.max_iter;
-  r.sched = p->prec == POLAR_SCHED_BF16_THEN_X3 ? 1 : 0;
+  r.sched = p->prec == POLAR_SCHED_BF16_THEN_X3 ? 1 : p->prec == POLAR_SCHED_FP8_BF16_X3 ? 2 : 0;
+  r.fp8_switch = p->opt.fp8_switch_residual;
   r.planes_fixed = p->P;
   r.n_pre = p->opt.precondition ? precond_steps(p->opt.s_minus, p->opt.s0) : 0;
   r.pre_a = 1.5 * sqrt(3.0) - p->opt.s_minus;
@@ -366,6 +380,23 @@ TcOperand op_planes(const uint16_t* planes, int64_t rows, int64_t cols, int64_t 
 
 cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
   const uint16_t* Xk = p->Xp[k & 1];
+  if (rule.sched == 2) {
+    // FP8 phase: X_k quantized per 128 x 128 tile, its Gram from that one plane (both launches are
+    // enqueued; the one for the phase that is not current returns at once)
+    cudaError_t e = launch_quantize_e4m3_planes(Xk, p->ldp, p->xps, p->m, p->n, p->Xq, p->ldp, p->st, s);
+    if (e != cudaSuccess) return e;
+    TcArgs q{};
+    q.M = p->n; q.N = p->n; q.K = p->m;
+    q.a = op_planes(p->Xq, p->m, p->n, p->ldp, p->xps, 0);
+    q.b = q.a;
+    q.nplanes = 1;
+    q.epi = TC_EPI_GRAM; q.triangular = 1;
+    q.out_planes = p->Gp; q.ldo = p->ldp; q.out_plane_stride = p->gps; q.out_nplanes = kStoredPlanes;
+    q.partials = p->partials; q.st = p->st;
+    q.planes_dyn = &p->st->fp8_on;
+    if ((e = launch_tc_gemm(q, s)) != cudaSuccess) return e;
+    p->launches += 2;
+  }
   TcArgs g{};
   g.M = p->n; g.N = p->n; g.K = p->m;
   g.a = op_planes(Xk, p->m, p->n, p->ldp, p->xps, 0);
@@ -388,6 +419,23 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
 }
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
+  if (rule.sched == 2) {
+    // FP8 phase: X_k (quantized with the Gram) times the quantized G
+    cudaError_t e = launch_quantize_e4m3_planes(p->Gp, p->ldp, p->gps, p->n, p->n, p->Gq, p->ldp, p->st, s);
+    if (e != cudaSuccess) return e;
+    TcArgs q{};
+    q.M = p->m; q.N = p->n; q.K = p->n;
+    q.a = op_planes(p->Xq, p->m, p->n, p->ldp, p->xps, 1);
+    q.b = op_planes(p->Gq, p->n, p->n, p->ldp, p->gps, 0);
+    q.nplanes = 1;
+    q.epi = TC_EPI_NS;
+    q.x_planes = p->Xp[k & 1]; q.ldxp = p->ldp; q.x_plane_stride = p->xps;
+    q.out_planes = p->Xp[(k + 1) & 1]; q.ldo = p->ldp; q.out_plane_stride = p->xps; q.out_nplanes = kStoredPlanes;
+    q.st = p->st;
+    q.planes_dyn = &p->st->fp8_on;
+    if ((e = launch_tc_gemm(q, s)) != cudaSuccess) return e;
+    p->launches += 2;
+  }
   TcArgs u{};
   u.M = p->m; u.N = p->n; u.K = p->n;
   u.a = op_planes(p->Xp[k & 1], p->m, p->n, p->ldp, p->xps, 1);
@@ -418,7 +466,8 @@ polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U
   // ||A||_F and X_0 = A / ||A||_F (+ planes of X_0)
   int fb = frob_partials_blocks(m, n);
   CK(launch_frob_partials(A, m, n, lda, p->partials, fb, s));
-  CK(launch_norm_finalize(p->partials, fb, p->st, 1.0 / sqrt((double)n), rule.sched ? 1 : p->P, s));
+  CK(launch_norm_finalize(p->partials, fb, p->st, 1.0 / sqrt((double)n),
+                          rule.sched == 2 ? 0 : rule.sched == 1 ? 1 : p->P, rule.sched == 2 ? 1 : 0, s));
   if (p->P == 0)
     CK(launch_scale_split(A, lda, m, n, p->st, true, p->X[0], p->ldx, nullptr, 0, 0, 0, s));
   else
@@ -548,7 +597,7 @@ polar_status_t polar_plan_create(polar_plan_t* plan, int64_t m, int64_t n, const
   if (o) opt = *o; else polar_default_options(&opt);
   normalize_options(opt);
   int prec = resolve_prec(opt.prec, n);
-  if (prec == POLAR_TF32X3 || prec == POLAR_SCHED_FP8_BF16_X3) return POLAR_ENOTSUP;
+  if (prec == POLAR_TF32X3) return POLAR_ENOTSUP;
   if (prec < 0 || prec > POLAR_BF16) return POLAR_EINVAL;
   int sms = 0;
   if (!device_ok(&sms)) { cudaGetLastError(); return POLAR_ECUDA; }
@@ -807,7 +856,7 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
     if (launch_tc_gemm(g, s) != cudaSuccess) break;
     if (launch_mirror_f32(C, ldc, M, nullptr, s) != cudaSuccess) break;
     if (launch_frob_partials(C, M, M, ldc, part, fb, s) != cudaSuccess) break;
-    if (launch_norm_finalize(part, fb, st, 1.0, P, s) != cudaSuccess) break;
+    if (launch_norm_finalize(part, fb, st, 1.0, P, 0, s) != cudaSuccess) break;
     // X_0 = A^T / a; the update X' = 2 X - X (A X)
     if (launch_transpose_scale_split(A, lda, N, M, st, xp[0], lpx, sx, s) != cudaSuccess) break;
     if (launch_inverse_init(st, s) != cudaSuccess) break;
@@ -962,4 +1011,14 @@ extern "C" polar_status_t polar_chebyshev(const float* A, int64_t n, int64_t lda
   cudaFree(ws);
   if (ret == POLAR_ECUDA) cudaGetLastError();
   return ret;
+}
+
+extern "C" polar_status_t polar_quantize_e4m3(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y,
+                                             int64_t ldy, polar_stream_t stream) {
+  if (rows < 0 || cols < 0) return POLAR_EINVAL;
+  if (rows == 0 || cols == 0) return POLAR_OK;
+  if (!X || !Y || ldx < cols || ldy < cols) return POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  return launch_quantize_e4m3_f32(X, ldx, rows, cols, Y, ldy, (cudaStream_t)stream) == cudaSuccess ? POLAR_OK
+                                                                                                  : POLAR_ECUDA;
 }

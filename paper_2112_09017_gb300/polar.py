@@ -29,7 +29,7 @@ class polar_options_t(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int), ("stagnation", C.c_double),
                 ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int),
                 ("precondition", C.c_int), ("s_minus", C.c_double), ("s0", C.c_double),
-                ("small_onchip", C.c_int)]
+                ("fp8_switch_residual", C.c_double), ("small_onchip", C.c_int)]
 
 
 class polar_info_t(C.Structure):
@@ -84,6 +84,7 @@ def load():
         "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
         "polar_ns_inverse": (i32, [vp, i64, i64, i64, vp, i64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
         "polar_chebyshev_nodes": (i32, [f64, f64, i32, C.POINTER(f64)]),
+        "polar_quantize_e4m3": (i32, [vp, i64, i64, i64, vp, i64, vp]),
         "polar_chebyshev_fit": (i32, [C.POINTER(f64), i32, C.POINTER(f64)]),
         "polar_chebyshev": (i32, [vp, i64, i64, f64, f64, C.POINTER(f64), i32, vp, i64, i32, vp]),
         "polar_device_query": (i32, [C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
@@ -242,6 +243,19 @@ def polar_ns_inverse(A, X, prec=POLAR_BF16X6, max_iter=100, stream=None, raw_sta
     if not raw_status and r not in (POLAR_OK, POLAR_NOT_CONVERGED):
         raise PolarError(r, "polar_ns_inverse")
     return {"status": r, "iters": it.value, "delta": d.value}
+
+
+def polar_quantize_e4m3(X, Y=None, stream=None):
+    """Y = s * e4m3(X / s) per 128 x 128 tile (the FP8 schedule's operand rounding); returns Y."""
+    import torch
+    _check_f32_2d(X, "X")
+    if Y is None:
+        Y = torch.empty_like(X)
+    _check_f32_2d(Y, "Y")
+    r = load().polar_quantize_e4m3(_ptr(X), X.shape[0], X.shape[1], X.stride(0), _ptr(Y), Y.stride(0), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_quantize_e4m3")
+    return Y
 
 
 def polar_chebyshev_nodes(a, b, degree):
