@@ -91,6 +91,10 @@ typedef struct {
   double s_minus;          /* preconditioning threshold; <= 0 means 0.1 */
   double s0;               /* estimate of the smallest singular value of A / ||A||_F; <= 0 means 2^-23 */
   double fp8_switch_residual; /* SCHED_FP8_BF16_X3: residual below which the FP8 phase ends; <= 0 means 0.5 */
+  int batched_tile_n;      /* batched plans: width of the grouped launches' output tiles, 256 (0 means 256:
+                              one epilogue group, as in the single solve) or 128 (two epilogue groups on
+                              alternate tiles, so that one tile's output step can overlap the next tile's
+                              products; measured no faster on the 4096-problem configuration) */
   int small_onchip;        /* batched plans with a fixed plane count: nonzero (the default) solves every
                               problem with n <= 128 and m <= 256 in one CTA that keeps X, G and the
                               accumulators on its SM for the whole loop; 0 sends them through the

@@ -254,6 +254,7 @@ struct BatchedPlan {
   TcTile* upd_t = nullptr;
   TcTile* h_t = nullptr;
   int64_t n_gram_t = 0, n_upd_t = 0, n_h_t = 0;
+  int tile_n = 256;                // width of the grouped launches' tiles (options.batched_tile_n)
   OcTask* oc_tasks = nullptr;      // problems solved on one SM each (largest first)
   int n_oc = 0;
   int32_t* iters_scratch = nullptr;
@@ -281,19 +282,19 @@ polar_status_t b_alloc(BatchedPlan* b, size_t bytes, void** out) {
   return POLAR_OK;
 }
 
-int64_t tri_tiles_h(int64_t tm, int64_t tn) { return (tn - 1) * tn + std::min(2 * tn, tm); }
 
 // Tile table: problems by decreasing work, each problem's tiles contiguous
 // (neighbouring CTAs of a wave share that problem's operand panels in L2).
 void build_tiles(const std::vector<int>& order, const std::vector<int64_t>& rows, const std::vector<int64_t>& cols,
-                 bool tri, std::vector<TcTile>& out, std::vector<int>* ntiles_of) {
+                 bool tri, int tile_n, std::vector<TcTile>& out, std::vector<int>* ntiles_of) {
   out.clear();
   for (int p : order) {
-    const int64_t tm = (rows[p] + kBM - 1) / kBM, tn = (cols[p] + kBN - 1) / kBN;
+    const int64_t tm = (rows[p] + kBM - 1) / kBM, tn = (cols[p] + tile_n - 1) / tile_n;
     int local = 0;
     if (tri) {
       for (int64_t bj = 0; bj < tn; ++bj)
-        for (int64_t bi = 0; bi < std::min(2 * bj + 2, tm); ++bi) out.push_back({p, (int32_t)bi, (int32_t)bj, local++});
+        for (int64_t bi = 0; bi < std::min((bj + 1) * tile_n / kBM, tm); ++bi)   // rows that reach the diagonal
+          out.push_back({p, (int32_t)bi, (int32_t)bj, local++});
     } else {
       for (int64_t bi = 0; bi < tm; ++bi)
         for (int64_t bj = 0; bj < tn; ++bj) out.push_back({p, (int32_t)bi, (int32_t)bj, local++});
@@ -331,6 +332,7 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   // the grouped loop, unless every problem was solved on-chip
   for (int k = 0; k <= b->opt.max_iter && b->n_gram_t > 0; ++k) {
     TcGroupLaunch g{};
+    g.tile_n = b->tile_n;
     g.nplanes = b->P;
     g.epi = TC_EPI_GRAM; g.a_mn = 1; g.b_mn = 1;
     g.tiles = b->gram_t; g.ntiles = b->n_gram_t; g.entries = b->gram_e[k & 1];
@@ -344,6 +346,7 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
     BK_(cudaGetLastError());
     if (k == b->opt.max_iter) break;
     TcGroupLaunch u{};
+    u.tile_n = b->tile_n;
     u.nplanes = b->P;
     u.epi = TC_EPI_NS; u.a_mn = 0; u.b_mn = 1;
     u.tiles = b->upd_t; u.ntiles = b->n_upd_t; u.entries = b->upd_e[k & 1];
@@ -355,6 +358,7 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   b_select_h_kernel<<<count, 64, 0, s>>>(b->h2_e, b->h_e, b->st_d, count);
   BK_(cudaGetLastError());
   TcGroupLaunch h{};
+  h.tile_n = b->tile_n;
   h.nplanes = b->P;
   h.epi = TC_EPI_STORE; h.a_mn = 1; h.b_mn = 1;
   h.tiles = b->h_t; h.ntiles = b->n_h_t; h.entries = b->h_e;
@@ -381,6 +385,7 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   b->opt = opt;
   b->prec = prec;
   b->P = prec == POLAR_BF16X6 ? 3 : (prec == POLAR_BF16X3 || prec == POLAR_SCHED_BF16_THEN_X3) ? 2 : 1;
+  b->tile_n = opt.batched_tile_n == 128 ? 128 : 256;
   b->m.assign(m, m + count);
   b->n.assign(n, n + count);
   polar_status_t r = POLAR_OK;
@@ -415,9 +420,9 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   std::vector<int> order_tc, order_oc;
   for (int p : order) (oc_ok && onchip_fits(m[p], n[p]) ? order_oc : order_tc).push_back(p);
   std::vector<TcTile> gram_t, upd_t, h_t;
-  build_tiles(order_tc, b->n, b->n, true, gram_t, &ntg);
-  build_tiles(order_tc, b->m, b->n, false, upd_t, nullptr);
-  build_tiles(order, b->n, b->n, false, h_t, nullptr);
+  build_tiles(order_tc, b->n, b->n, true, b->tile_n, gram_t, &ntg);
+  build_tiles(order_tc, b->m, b->n, false, b->tile_n, upd_t, nullptr);
+  build_tiles(order, b->n, b->n, false, b->tile_n, h_t, nullptr);
   size_t part_count = 0;
   for (int p = 0; p < count; ++p) part_count += (size_t)ntg[p] * kEpiWarps;
 

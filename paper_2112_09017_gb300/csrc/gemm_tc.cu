@@ -65,7 +65,7 @@ constexpr int BM = 128, BN = 256, BK = 32;   // two K=16 MMA steps per k-stage
 constexpr int NTHREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr uint32_t A_PLANE = BM * BK * 2;  // 8 KiB per plane per stage
-constexpr uint32_t B_PLANE = BN * BK * 2;  // 16 KiB
+constexpr uint32_t B_PLANE = BN * BK * 2;  // 16 KiB (128 x 256 tiles)
 // MN-major operands: 64-column chunks of BK rows x 128 bytes (128-byte swizzle)
 constexpr uint32_t MN_CHUNK = 64 * BK * 2;
 // K-major operands: rows of BK elements (BK * 2 bytes), swizzle of that width, 8-row groups
@@ -73,20 +73,25 @@ constexpr uint32_t KM_SBO = 8 * BK * 2;
 constexpr uint32_t KM_SWZ = BK == 16 ? 6 : BK == 32 ? 4 : 2;   // descriptor codes: 32, 64, 128-byte swizzle
 constexpr uint32_t TMEM_COLS = 512;        // two 128 x 256 FP32 slice accumulators
 
-template <int P>
+// Tile width TN: 256 (one epilogue group of eight warps, two 256-column TMEM slice buffers)
+// or 128 (two epilogue groups of four warps taking alternate tiles, two 128-column slice
+// buffers each, so that one group's output step overlaps the next tile's MMAs).
+template <int P, int TN = BN>
 struct Cfg {
-  static constexpr int STAGES = (P == 3 ? 6 : (P == 2 ? 9 : 16)) * 16 / BK;
+  static constexpr int STAGES = TN == BN ? (P == 3 ? 6 : (P == 2 ? 9 : 16)) * 16 / BK : (P == 3 ? 4 : (P == 2 ? 6 : 12));
+  static constexpr int NBUF = TN == BN ? 2 : 4;          // TMEM slice buffers of TN columns
+  static constexpr int GROUP_WARPS = TN == BN ? EPI_WARPS : EPI_WARPS / 2;
   static constexpr uint32_t A_BYTES = P * A_PLANE;
-  static constexpr uint32_t B_BYTES = P * B_PLANE;
+  static constexpr uint32_t B_BYTES = P * TN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr uint32_t NBARS = 2 * STAGES + 5;
+  static constexpr uint32_t NBARS = 2 * STAGES + 2 * NBUF + 1;
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 + 8 * NBARS + 16;
 };
 
-// Instruction descriptor: D = F32, A = B = BF16, M = 128, N = 256, majors as given.
-__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn) {
+// Instruction descriptor: D = F32, A = B = BF16, M = 128, N = tn, majors as given.
+__host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn, int tn = BN) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 // Plane pairs of the split product in issue order for `np` planes: the smallest
@@ -257,10 +262,10 @@ struct GroupSrc {
   }
 };
 
-template <int P, bool A_MN, bool B_MN, class Src>
+template <int P, bool A_MN, bool B_MN, int TN, class Src>
 __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, Bars br, volatile int* abort_flag,
                                            int withhold) {
-  using C = Cfg<P>;
+  using C = Cfg<P, TN>;
   constexpr int S = C::STAGES;
   if (withhold) return;  // test hook: no copies are issued, the consumers' bounded waits expire
   int stage = 0;
@@ -276,7 +281,7 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(c.mb)) : "memory");
       last_a = c.ma;
     }
-    const int m0 = (int)(c.bi * BM), n0 = (int)(c.bj * BN);
+    const int m0 = (int)(c.bi * BM), n0 = (int)(c.bj * TN);
     for (int64_t kb = 0; kb < c.nk; ++kb) {
       if (!mbar_wait(br.empty0 + 8 * stage, phase ^ 1u, abort_flag)) { ok = false; break; }
       const uint32_t fb = br.full0 + 8 * stage;
@@ -294,7 +299,7 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
       }
       if (B_MN) {
 #pragma unroll
-        for (int cc = 0; cc < BN / 64; ++cc) tma_load_3d(b_dst + cc * P * MN_CHUNK, c.mb, fb, n0 + 64 * cc, k0, 0);
+        for (int cc = 0; cc < TN / 64; ++cc) tma_load_3d(b_dst + cc * P * MN_CHUNK, c.mb, fb, n0 + 64 * cc, k0, 0);
       } else {
         tma_load_3d(b_dst, c.mb, fb, k0, n0, 0);
       }
@@ -308,24 +313,25 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
 
 // The NP-plane passes on one k-stage: descriptors are the stage-0 bases plus
 // compile-time offsets (the start-address field is the low 14 bits, address / 16).
-template <int P, bool A_MN, bool B_MN, int NP>
+template <int P, bool A_MN, bool B_MN, int NP, int TN = BN>
 __device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t first_acc) {
-  constexpr uint32_t idesc = make_idesc(A_MN, B_MN);
+  constexpr uint32_t idesc = make_idesc(A_MN, B_MN, TN);
+  constexpr uint32_t B_PL = TN * BK * 2;
 #pragma unroll
   for (int ps = 0; ps < passes_for(NP); ++ps) {
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
       const uint32_t aoff = A_MN ? pass_a(NP, ps) * MN_CHUNK + kk * 2048 : pass_a(NP, ps) * A_PLANE + kk * 32;
-      const uint32_t boff = B_MN ? pass_b(NP, ps) * MN_CHUNK + kk * 2048 : pass_b(NP, ps) * B_PLANE + kk * 32;
+      const uint32_t boff = B_MN ? pass_b(NP, ps) * MN_CHUNK + kk * 2048 : pass_b(NP, ps) * B_PL + kk * 32;
       tc_mma(d_tmem, a_desc + (aoff >> 4), b_desc + (boff >> 4), idesc, (ps == 0 && kk == 0) ? first_acc : 1u);
     }
   }
 }
 
-template <int P, bool A_MN, bool B_MN, class Src>
+template <int P, bool A_MN, bool B_MN, int TN, class Src>
 __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32_t tmem_base, Bars br,
                                       volatile int* abort_flag, int SL, int pu) {
-  using C = Cfg<P>;
+  using C = Cfg<P, TN>;
   constexpr int S = C::STAGES;
   const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * MN_CHUNK, 1024, 2)
                                 : smem_desc(smem_base, 16, KM_SBO, KM_SWZ);
@@ -333,29 +339,37 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
                                 : smem_desc(smem_base + C::A_BYTES, 16, KM_SBO, KM_SWZ);
   int stage = 0;
   uint32_t phase = 0;
-  int buf = 0;
-  uint32_t buf_phase = 0;
+  // slice buffers: one pair for TN = 256; with TN = 128 a pair per epilogue group, the groups
+  // taking alternate tiles (each pair keeps its own position and phase)
+  int gbuf[2] = {0, 0};
+  uint32_t gphase[2] = {0u, 0u};
+  int64_t ntile = 0;
   bool ok = true;
   for (int64_t t = blockIdx.x; t < src.ntiles && ok; t += gridDim.x) {
     TileCtx c;
     if (!src.get(t, c)) continue;
+    const int grp = TN == BN ? 0 : (int)(ntile++ & 1);
+    int& buf = gbuf[grp];
+    uint32_t& buf_phase = gphase[grp];
     int kin = 0;  // k-stage index within the current slice
     for (int64_t kb = 0; kb < c.nk; ++kb) {
       // SL k-stages into a fresh slice buffer, then published to the epilogue
       const bool slice_start = kin == 0;
       const bool slice_end = kin == SL - 1 || kb == c.nk - 1;
-      if (slice_start && !mbar_wait(br.tempty0 + 8 * buf, buf_phase ^ 1u, abort_flag)) { ok = false; break; }
+      const int bslot = 2 * grp + buf;
+      if (slice_start && !mbar_wait(br.tempty0 + 8 * bslot, buf_phase ^ 1u, abort_flag)) { ok = false; break; }
       if (!mbar_wait(br.full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(bslot * TN);
       const uint64_t soff = (uint64_t)((stage * C::STAGE_BYTES) >> 4);
       const uint32_t first_acc = slice_start ? 0u : 1u;
-      if (pu == P) issue_stage<P, A_MN, B_MN, P>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
-      else if (pu == 2) issue_stage<P, A_MN, B_MN, (P >= 2 ? 2 : P)>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
-      else issue_stage<P, A_MN, B_MN, 1>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      if (pu == P) issue_stage<P, A_MN, B_MN, P, TN>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      else if (pu == 2)
+        issue_stage<P, A_MN, B_MN, (P >= 2 ? 2 : P), TN>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      else issue_stage<P, A_MN, B_MN, 1, TN>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
       tc_commit(br.empty0 + 8 * stage);
       if (slice_end) {
-        tc_commit(br.tfull0 + 8 * buf);
+        tc_commit(br.tfull0 + 8 * bslot);
         if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
         kin = 0;
       } else {
@@ -369,18 +383,22 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
   mbar_drain(br.drain, 0);
 }
 
-template <int EPI, class Src>
+template <int EPI, int TN, class Src>
 __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, Bars br, volatile int* abort_flag,
                                            int SL, int warp, int lane) {
-  const int q = warp & 3;                  // TMEM lane quarter this warp may access
-  const int half = (warp - 2) >> 2;        // which 128 of the tile's 256 columns
+  const int q = warp & 3;                              // TMEM lane quarter this warp may access
+  const int half = TN == BN ? (warp - 2) >> 2 : 0;     // TN = 256: which 128 of the tile's columns
+  const int grp = TN == BN ? 0 : (warp - 2) >> 2;      // TN = 128: the group (alternate tiles)
+  const int gw = TN == BN ? warp - 2 : (warp - 2) & 3; // this warp's partials slot within the tile
   const int row_in_tile = q * 32 + lane;
   const uint32_t t_lane = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
   int buf = 0;
   uint32_t buf_phase = 0;
+  int64_t ntile = 0;
   for (int64_t t = blockIdx.x; t < src.ntiles; t += gridDim.x) {
     TileCtx ctx;
     if (!src.get(t, ctx)) continue;
+    if (TN != BN && (int)(ntile++ & 1) != grp) continue;   // the other group's tile
     const TcArgs& p = *ctx.args;
     const int64_t nslices = (ctx.nk + SL - 1) / SL;
     constexpr bool NS = EPI == TC_EPI_NS || EPI == TC_EPI_NS_STEP;
@@ -391,22 +409,23 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
     bool ok = true;
     for (int64_t sl = 0; sl < nslices; ++sl) {
-      if (!mbar_wait(br.tfull0 + 8 * buf, buf_phase, abort_flag)) { ok = false; break; }
+      const int bslot = 2 * grp + buf;
+      if (!mbar_wait(br.tfull0 + 8 * bslot, buf_phase, abort_flag)) { ok = false; break; }
       tc_fence_after();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         float v[16];
-        tmem_ld16(t_lane + (uint32_t)(buf * BN + c * 16), v);
+        tmem_ld16(t_lane + (uint32_t)(bslot * TN + c * 16), v);
         add16_packed(&acc[c * 16], v);   // round-to-nearest promotion
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(br.tempty0 + 8 * buf);
+      if (lane == 0) mbar_arrive(br.tempty0 + 8 * bslot);
       if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
       if ((NS || CLEN) && sl == (nslices > 1 ? nslices - 2 : 0)) {
         // the output step reads this row's 128 columns of X_k's (or Z's) three planes: pull them into L2 now
         const int64_t r = ctx.bi * BM + row_in_tile;
-        const int64_t c0 = ctx.bj * BN + half * 128;
+        const int64_t c0 = ctx.bj * TN + half * 128;
         if (r < p.M && c0 < p.N) {
           const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
 #pragma unroll
@@ -428,7 +447,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     float d2 = 0.f, x2 = 0.f;  // NS_STEP: sum (x' - x)^2 and sum x'^2 over this thread's row chunk
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int64_t c0 = ctx.bj * BN + half * 128 + c * 32;
+      const int64_t c0 = ctx.bj * TN + half * 128 + c * 32;
       float* v = &acc[c * 32];
       if (!row_ok || c0 >= p.N) continue;
       const bool full_chunk = c0 + 32 <= p.N;
@@ -558,7 +577,10 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     if (EPI == TC_EPI_GRAM) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-      if (lane == 0) p.partials[ctx.part + (warp - 2)] = part;
+      if (lane == 0) {
+        p.partials[ctx.part + gw] = part;
+        if (TN != BN) p.partials[ctx.part + 4 + gw] = 0.0;   // a 128-wide tile fills four of its eight slots
+      }
     }
     if (STEP) {
       double a = d2, b = x2;
@@ -568,18 +590,22 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
         b += __shfl_down_sync(0xffffffffu, b, o);
       }
       if (lane == 0) {
-        p.partials[2 * (ctx.part + (warp - 2))] = a;
-        p.partials[2 * (ctx.part + (warp - 2)) + 1] = b;
+        p.partials[2 * (ctx.part + gw)] = a;
+        p.partials[2 * (ctx.part + gw) + 1] = b;
+        if (TN != BN) {
+          p.partials[2 * (ctx.part + 4 + gw)] = 0.0;
+          p.partials[2 * (ctx.part + 4 + gw) + 1] = 0.0;
+        }
       }
     }
   }
 }
 
 // Shared prologue/epilogue of both launch forms; `Src` supplies the tiles.
-template <int P, bool A_MN, bool B_MN, int EPI, class Src>
+template <int P, bool A_MN, bool B_MN, int EPI, int TN, class Src>
 __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, int SL, const int* planes_dyn,
                                         int withhold) {
-  using C = Cfg<P>;
+  using C = Cfg<P, TN>;
   constexpr int S = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -591,8 +617,8 @@ __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_w
   br.full0 = smem_u32(&bars[0]);
   br.empty0 = smem_u32(&bars[S]);
   br.tfull0 = smem_u32(&bars[2 * S]);
-  br.tempty0 = smem_u32(&bars[2 * S + 2]);
-  br.drain = smem_u32(&bars[2 * S + 4]);
+  br.tempty0 = smem_u32(&bars[2 * S + C::NBUF]);
+  br.drain = smem_u32(&bars[2 * S + 2 * C::NBUF]);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -600,9 +626,9 @@ __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_w
       mbar_init(br.full0 + 8 * s, 1);
       mbar_init(br.empty0 + 8 * s, 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < C::NBUF; ++a) {
       mbar_init(br.tfull0 + 8 * a, 1);
-      mbar_init(br.tempty0 + 8 * a, EPI_WARPS);
+      mbar_init(br.tempty0 + 8 * a, C::GROUP_WARPS);
     }
     mbar_init(br.drain, 1);
     *abort_flag = 0;
@@ -621,14 +647,14 @@ __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_w
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) role_producer<P, A_MN, B_MN>(src, smem_base, br, abort_flag, withhold);
+    if (lane == 0) role_producer<P, A_MN, B_MN, TN>(src, smem_base, br, abort_flag, withhold);
   } else if (warp == 1) {
     if (lane == 0) {
       const int pu = planes_dyn ? min(max(*planes_dyn, 1), P) : P;
-      role_mma<P, A_MN, B_MN>(src, smem_base, tmem_base, br, abort_flag, SL, pu);
+      role_mma<P, A_MN, B_MN, TN>(src, smem_base, tmem_base, br, abort_flag, SL, pu);
     }
   } else {
-    role_epilogue<EPI>(src, tmem_base, br, abort_flag, SL, warp, lane);
+    role_epilogue<EPI, TN>(src, tmem_base, br, abort_flag, SL, warp, lane);
   }
 
   tc_fence_before();
@@ -664,18 +690,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   src.ntiles = ntiles;
   src.nk = (p.K + BK - 1) / BK;
   src.tri = p.triangular != 0;
-  tc_body<P, A_MN, B_MN, EPI>(src, p.st, nullptr, p.slice_stages > 0 ? p.slice_stages : 1, p.planes_dyn,
+  tc_body<P, A_MN, B_MN, EPI, BN>(src, p.st, nullptr, p.slice_stages > 0 ? p.slice_stages : 1, p.planes_dyn,
                               p.withhold_tma);
 }
 
-template <int P, bool A_MN, bool B_MN, int EPI>
+template <int P, bool A_MN, bool B_MN, int EPI, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_grouped_kernel(const __grid_constant__ TcGroupLaunch g) {
   if (g.done && *g.done) return;
   GroupSrc src;
   src.tiles = g.tiles;
   src.entries = g.entries;
   src.ntiles = g.ntiles;
-  tc_body<P, A_MN, B_MN, EPI>(src, nullptr, g.err, g.slice_stages > 0 ? g.slice_stages : 1, g.planes_dyn,
+  tc_body<P, A_MN, B_MN, EPI, TN>(src, nullptr, g.err, g.slice_stages > 0 ? g.slice_stages : 1, g.planes_dyn,
                               g.withhold_tma);
 }
 
@@ -848,22 +874,29 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
 namespace polar {
 namespace {
 
-template <int P, bool A_MN, bool B_MN, int EPI>
+template <int P, bool A_MN, bool B_MN, int EPI, int TN>
 cudaError_t launch_grouped_t(const TcGroupLaunch& g, cudaStream_t s) {
-  auto k = tc_gemm_grouped_kernel<P, A_MN, B_MN, EPI>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P>::SMEM);
+  auto k = tc_gemm_grouped_kernel<P, A_MN, B_MN, EPI, TN>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<P, TN>::SMEM);
   if (e != cudaSuccess) return e;
   int64_t grid = g.ntiles < sm_count() ? g.ntiles : sm_count();
   if (grid < 1) return cudaSuccess;
-  k<<<(unsigned)grid, NTHREADS, Cfg<P>::SMEM, s>>>(g);
+  k<<<(unsigned)grid, NTHREADS, Cfg<P, TN>::SMEM, s>>>(g);
   return cudaGetLastError();
+}
+
+template <int P, int TN>
+cudaError_t dispatch_grouped_tn(const TcGroupLaunch& g, cudaStream_t s) {
+  if (g.epi == TC_EPI_NS && !g.a_mn && g.b_mn) return launch_grouped_t<P, false, true, TC_EPI_NS, TN>(g, s);
+  if (g.epi == TC_EPI_GRAM && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_GRAM, TN>(g, s);
+  if (g.epi == TC_EPI_STORE && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_STORE, TN>(g, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int P>
 cudaError_t dispatch_grouped(const TcGroupLaunch& g, cudaStream_t s) {
-  if (g.epi == TC_EPI_NS && !g.a_mn && g.b_mn) return launch_grouped_t<P, false, true, TC_EPI_NS>(g, s);
-  if (g.epi == TC_EPI_GRAM && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_GRAM>(g, s);
-  if (g.epi == TC_EPI_STORE && g.a_mn && g.b_mn) return launch_grouped_t<P, true, true, TC_EPI_STORE>(g, s);
+  if (g.tile_n == 128) return dispatch_grouped_tn<P, 128>(g, s);
+  if (g.tile_n == 0 || g.tile_n == BN) return dispatch_grouped_tn<P, BN>(g, s);
   return cudaErrorInvalidValue;
 }
 

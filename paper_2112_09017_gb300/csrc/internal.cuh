@@ -189,6 +189,7 @@ struct TcGroupLaunch {
   const int* planes_dyn;
   int slice_stages;
   int withhold_tma;                       // test hook, as in TcArgs
+  int tile_n;                             // 256 (0 also) or 128: the tiles' width; the table must match
 };
 cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g, cudaStream_t s);
 // Fills entry->map_a / map_b for the operands of entry->args (host side).

@@ -29,7 +29,7 @@ class polar_options_t(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int), ("stagnation", C.c_double),
                 ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int),
                 ("precondition", C.c_int), ("s_minus", C.c_double), ("s0", C.c_double),
-                ("fp8_switch_residual", C.c_double), ("small_onchip", C.c_int)]
+                ("fp8_switch_residual", C.c_double), ("batched_tile_n", C.c_int), ("small_onchip", C.c_int)]
 
 
 class polar_info_t(C.Structure):

@@ -133,3 +133,37 @@ def test_onchip_bounded_wait_expires_and_context_survives(lib, monkeypatch):
     (Us, Hs, iters, res), = _run(lib, mats)
     assert np.all(iters >= 0)
     assert metrics(mats[1], Us[1], Hs[1])["orth"] <= 5e-6
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_grouped_tile_widths_match_oracle(lib, tile_n):
+    """The grouped launches with 128-wide tiles (two epilogue groups on alternate tiles) and
+    with 256-wide tiles: parity with the oracle on uneven problems beyond the on-chip sizes."""
+    import torch
+    sizes = [(300, 300), (520, 260), (257, 129), (400, 200), (1000, 500), (129, 129), (640, 640)]
+    kap = [1e3, 1e2, 1e2, 1e2, 1e3, 10.0, 1e2]
+    mats = _mats(sizes, kap, 1000)
+    ms = [a.shape[0] for a in mats]
+    ns = [a.shape[1] for a in mats]
+    o = lib.polar_default_options()
+    o.batched_tile_n = tile_n
+    plan = lib.polar_batched_plan_create(ms, ns, o)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    outs = []
+    for _ in range(2):
+        Us = [torch.full((m, n), 7.0, device="cuda") for m, n in zip(ms, ns)]
+        Hs = [torch.full((n, n), 7.0, device="cuda") for n in ns]
+        it = torch.zeros(len(mats), dtype=torch.int32, device="cuda")
+        lib.polar_batched_run(plan, As, Us, Hs, 0.0, it, None)
+        torch.cuda.synchronize()
+        outs.append(([to_np(u) for u in Us], [to_np(h) for h in Hs], it.cpu().numpy()))
+    lib.polar_plan_destroy(plan)
+    (Us, Hs, iters), (Us2, Hs2, iters2) = outs
+    assert np.array_equal(iters, iters2)
+    for i, a in enumerate(mats):
+        assert np.array_equal(Us[i], Us2[i]) and np.array_equal(Hs[i], Hs2[i])
+        ref = ns_polar(a, tol=1e-12, count_tol=1e-6)
+        assert abs(iters[i] - ref["iters_at"]) <= 1, (sizes[i], iters[i], ref["iters_at"])
+        met = metrics(a, Us[i], Hs[i], ref["U"])
+        assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, (sizes[i], met)
+        assert met["fwd"] <= max(1e-7 * kap[i], 1e-6), (sizes[i], met)
