@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["bf16_rne_bits", "bf16_rne", "split_planes", "plane_pairs", "emulated_matmul",
-           "bits_to_float", "e4m3_rne", "quantize_tiles_e4m3", "E4M3_MAX"]
+           "bits_to_float", "e4m3_rne", "quantize_tiles_e4m3", "E4M3_MAX", "ns_polar_emulated"]
 
 PAIRS = {
     1: ((0, 0),),
@@ -126,3 +126,54 @@ def quantize_tiles_e4m3(x, tile: int = 128) -> np.ndarray:
                     s /= 2.0
             out[i:i + tile, j:j + tile] = (e4m3_rne(b / s).astype(np.float64) * s).astype(np.float32)
     return out
+
+
+# ---- the precision model of a whole solve ----
+
+def ns_polar_emulated(a, schedule: str = "bf16x6", tol: float = 1e-6, max_iter: int = 100,
+                      stagnation: float = 0.7, stag_floor: float = 1e-4, switch_residual: float = 1e-2,
+                      fp8_switch: float = 0.5) -> dict:
+    """The Newton-Schulz solve (Sec. III.D, the residual stop rule) with the products of a
+    precision schedule modelled: the iterate kept in float32 (the GPU keeps it as an exact
+    three-plane encoding), each product by ``emulated_matmul`` with the schedule's plane count
+    (FP8 phase: operands rounded by ``quantize_tiles_e4m3``, then one-plane products, which are
+    exact for such values), the update formed in float32, H = sym(U^T A) at the final plane count.
+    Schedules: "bf16x6", "bf16x3", "bf16", "bf16_then_x3", "fp8_bf16_x3". Returns U, H, iters,
+    status and the residual history."""
+    a32 = np.asarray(a, dtype=np.float32)
+    n = a32.shape[1]
+    fixed = {"bf16x6": 3, "bf16x3": 2, "bf16": 1}
+    planes_final = fixed.get(schedule, 2)
+    x = (a32.astype(np.float64) / np.linalg.norm(a32.astype(np.float64))).astype(np.float32)
+    fp8 = schedule == "fp8_bf16_x3"
+    planes = fixed.get(schedule, 1)
+    res, status, k = [], "not_converged", 0
+    while True:
+        xo = quantize_tiles_e4m3(x) if fp8 else x
+        g = emulated_matmul(xo.T.copy(), xo, 1 if fp8 else planes)
+        r = float(np.linalg.norm(g.astype(np.float64) - np.eye(n)) / np.sqrt(n))
+        res.append(r)
+        r2 = res[k - 2] if k >= 2 else 0.0
+        if not np.isfinite(r):
+            status = "nonfinite"
+            break
+        if r <= tol:
+            status = "converged"
+            break
+        if k >= 2 and r > stagnation * r2 and r < stag_floor:
+            break
+        if k >= max_iter:
+            break
+        if schedule in ("bf16_then_x3", "fp8_bf16_x3"):
+            if fp8 and not r > fp8_switch:
+                fp8 = False
+            planes = 1 if r > switch_residual else 2
+        if fp8:
+            p = emulated_matmul(quantize_tiles_e4m3(x), quantize_tiles_e4m3(g), 1)
+        else:
+            p = emulated_matmul(x, g, planes)
+        x = (np.float32(1.5) * x + np.float32(-0.5) * p).astype(np.float32)
+        k += 1
+    c = emulated_matmul(x.T.copy(), a32, planes_final).astype(np.float64)
+    h = 0.5 * (c + c.T)
+    return {"U": x, "H": h, "iters": k, "status": status, "residuals": res}
