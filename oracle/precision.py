@@ -66,10 +66,11 @@ def split_planes(x, p: int):
     """Split float32 x into p BF16 planes; returns a list of uint16 arrays."""
     rem = np.asarray(x, dtype=np.float32)
     planes = []
-    for _ in range(p):
-        b = bf16_rne_bits(rem)
-        planes.append(b)
-        rem = (rem - bits_to_float(b)).astype(np.float32)
+    with np.errstate(invalid="ignore"):   # inf - inf: a non-finite input leaves NaN in the lower planes
+        for _ in range(p):
+            b = bf16_rne_bits(rem)
+            planes.append(b)
+            rem = (rem - bits_to_float(b)).astype(np.float32)
     return planes
 
 
