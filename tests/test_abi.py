@@ -101,3 +101,32 @@ def test_chebyshev_host_setup_matches_oracle(built_lib):
     assert lib.polar_chebyshev_fit(bad, 1, out) == polar.POLAR_ENONFINITE
     coef = (ctypes.c_double * 2)(1.0, 2.0)
     assert lib.polar_chebyshev(None, 4, 4, -1.0, 1.0, coef, 1, None, 4, 1, None) == polar.POLAR_EINVAL
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of polar_options_t and polar_info_t have the C layout: a
+    program compiled against include/polar.h prints every field's offset and each
+    struct's size, which must equal what ctypes computes."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2112_09017_gb300 import polar
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "polar.h"', "int main(void) {"]
+    for struct in (polar.polar_options_t, polar.polar_info_t):
+        name = struct.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in struct._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = []
+    for struct in (polar.polar_options_t, polar.polar_info_t):
+        name = struct.__name__
+        want.append(f"{name} size {ctypes.sizeof(struct)}")
+        want += [f"{name} {field} {getattr(struct, field).offset}" for field, _ in struct._fields_]
+    assert [g for g in got if g] == want
