@@ -10,7 +10,9 @@ Modules:
   scalar      the scalar recurrences (Eqs. NS_scalar, a_def, RogueScalar) and
               the exact-arithmetic residual trajectory predicted from a spectrum
   jacobi_svd  one-sided Jacobi SVD, the independent checker on small inputs
-  precision   bit-level BF16 plane split and an emulator of split products
+  precision   bit-level BF16 plane split, an emulator of split products, FP8 E4M3
+              rounding with per-tile power-of-two scales, and the whole solve under
+              each precision schedule (the precision model)
   ns_inverse  the Newton-Schulz matrix inverse of Algorithm 2 and its trajectory
               predicted from a spectrum
   chebyshev   Chebyshev interpolation and Clenshaw summation of a matrix function
