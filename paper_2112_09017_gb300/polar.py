@@ -175,7 +175,22 @@ def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None):
 
 
 def polar_batched_run(plan, As, Us, Hs, tol=0.0, iters_dev=None, resid_dev=None, stream=None):
+    """Every problem of a batched plan: A[i] (m_i x n_i), U[i] (m_i x n_i), H[i] (n_i x n_i),
+    packed row-major float32 CUDA tensors; iters_dev (int32) and resid_dev (float64) device
+    arrays of at least len(As) entries, or None. Stream-asynchronous."""
+    import torch
     cnt = len(As)
+    if len(Us) != cnt or len(Hs) != cnt:
+        raise ValueError("As, Us and Hs must have the same length")
+    for i, (a, u, h) in enumerate(zip(As, Us, Hs)):
+        for t, name in ((a, "A"), (u, "U"), (h, "H")):
+            if t.dtype != torch.float32 or t.dim() != 2 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name}[{i}] must be a packed row-major 2-D float32 CUDA tensor")
+        if tuple(u.shape) != tuple(a.shape) or tuple(h.shape) != (a.shape[1], a.shape[1]):
+            raise ValueError(f"problem {i}: U must be m x n and H n x n for A of shape {tuple(a.shape)}")
+    for t, dt, name in ((iters_dev, torch.int32, "iters_dev"), (resid_dev, torch.float64, "resid_dev")):
+        if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() < cnt):
+            raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor of at least {cnt} entries")
     pa = (C.c_void_p * cnt)(*[a.data_ptr() for a in As])
     pu = (C.c_void_p * cnt)(*[u.data_ptr() for u in Us])
     ph = (C.c_void_p * cnt)(*[h.data_ptr() for h in Hs])

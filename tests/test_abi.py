@@ -130,3 +130,16 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         want.append(f"{name} size {ctypes.sizeof(struct)}")
         want += [f"{name} {field} {getattr(struct, field).offset}" for field, _ in struct._fields_]
     assert [g for g in got if g] == want
+
+
+def test_batched_run_binding_rejects_bad_arguments():
+    """The batched binding checks its tensors before any call into the library."""
+    torch = pytest.importorskip("torch")
+    from paper_2112_09017_gb300 import polar
+    a, h = torch.zeros(4, 3), torch.zeros(3, 3)
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(None, [a], [a], [])            # lengths differ
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(None, [a], [a], [h])           # host tensors
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(None, [a.double()], [a], [h])  # not float32

@@ -48,3 +48,34 @@ def test_polar_strided_views_and_guard_bands(lib, prec):
     ref = ns_polar(a, tol=1e-12, count_tol=1e-6)
     met = metrics(a, to_np(U), to_np(H), ref["U"])
     assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6 and met["fwd"] <= 1e-5, met
+
+
+def test_batched_outputs_stay_inside_their_problems(lib):
+    """Batched outputs packed into one sentinel-filled buffer with gaps between the
+    problems (on-chip and grouped members alike): every gap keeps its sentinel and
+    each problem's factors meet the bounds."""
+    import torch
+    sizes = [(64, 32), (300, 150), (96, 96), (520, 260), (256, 128), (129, 129)]
+    mats = [synth.matrix_with_spectrum(m, n, synth.logspace_spectrum(n, 1e-2), 20 + i)
+            for i, (m, n) in enumerate(sizes)]
+    gap = 37
+    total = sum(m * n + n * n + 2 * gap for m, n in sizes) + gap
+    buf = torch.full((total,), SENTINEL, dtype=torch.float32, device="cuda")
+    Us, Hs, spans, off = [], [], [], gap
+    for m, n in sizes:
+        Us.append(buf[off:off + m * n].view(m, n)); spans.append((off, off + m * n)); off += m * n + gap
+        Hs.append(buf[off:off + n * n].view(n, n)); spans.append((off, off + n * n)); off += n * n + gap
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    plan = lib.polar_batched_plan_create([m for m, _ in sizes], [n for _, n in sizes], lib.polar_default_options())
+    it = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+    lib.polar_batched_run(plan, As, Us, Hs, 0.0, it, None)
+    torch.cuda.synchronize()
+    lib.polar_plan_destroy(plan)
+    mask = torch.ones(total, dtype=torch.bool, device="cuda")
+    for lo, hi in spans:
+        mask[lo:hi] = False
+    assert bool(torch.all(buf[mask] == SENTINEL))
+    assert bool(torch.all(it >= 0))
+    for a, U, H in zip(mats, Us, Hs):
+        met = metrics(a, to_np(U), to_np(H))
+        assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, met
