@@ -3,20 +3,25 @@
 
 One step = one whole polar solve (||A||_F, X_0 = A/||A||_F, the Newton-Schulz loop
 to ||X^T X - I||_F / sqrt(n) <= tol, U and H = sym(U^T A)) of a seeded synthetic
-matrix with a prescribed spectrum, input resident in HBM.
+matrix with a prescribed spectrum, input resident in HBM. The default workload is the
+largest single-GPU one: 32768 x 32768, two-segment spectrum (kappa = 1e8), about 26 s
+per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload square8192_k1e4] [--prec bf16x6] [--no-plain] [--no-cpu]
+                  [--workload square32768_k1e8] [--prec bf16x6] [--no-plain] [--no-cpu]
                   [--batched 4096] [--no-precond] [--no-inverse] [--no-chebyshev]
+                  [--no-variants] [--no-legs]
 
-Beside the headline solve the line carries measured legs on the same shape: the plain FP32
-form, the preconditioned iteration (Algorithm 1), the Newton-Schulz inverse (Algorithm 2),
-a Chebyshev matrix function by Clenshaw summation, the batched configuration, and a batch of
-small problems (n on [64, 128]) solved one SM each, timed against the grouped tile path.
+Beside the headline solve: the same solve end to end through polar_run_host (host
+buffers), the plain FP32 form on the same input (one solve at the large size), a cuBLAS
+FP32 estimate, and the oracle on a bounded CPU sample. Then legs on the 8192 x 8192
+workload (fixed form, Algorithm 1, the reduced-precision variants, Algorithm 2, a
+Chebyshev function) and the batched configurations; their details go to stderr as one
+"legs: {...}" line and a few of their numbers into the JSON line.
 
-Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its own
-problem of the same size (independent replicas; the single solve does not shard),
-so `value` is the whole-job throughput and scaling is weak.
+Prints one JSON line (rank 0), floats to 4 significant digits. Under torchrun (N > 1)
+every rank solves its own problem of the same size (independent replicas; the single
+solve does not shard), so `value` is the whole-job throughput and scaling is weak.
 """
 from __future__ import annotations
 
@@ -34,7 +39,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "polar TFLOP/s & solves/s at ≤5e-6 orth error: mixed vs plain FP32, one GB300"
-DEFAULT_WORKLOAD = "square8192_k1e4"
+DEFAULT_WORKLOAD = "square32768_k1e8"   # the largest single-GPU configuration
+LEGS_WORKLOAD = "square8192_k1e4"        # shape of the extra legs (inverse, Chebyshev, variants, ...)
+CPU_PANEL_COLS = 4096                    # columns of the oracle's bounded sample of a large workload
 
 
 def algorithmic_flops(m, n, iters):
@@ -44,11 +51,16 @@ def algorithmic_flops(m, n, iters):
 
 
 def kernel_source_hash():
-    """First 16 hex digits of sha256 over the tensor-core kernel's sources."""
+    """First 16 hex digits of sha256 over the tensor-core kernel's sources (gemm_tc*.cu and the
+    headers they include, in name order)."""
+    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in ("gemm_tc.cu", "internal.cuh", "device_util.cuh", "tc_ptx.cuh"):
-        with open(os.path.join(ROOT, "paper_2112_09017_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2112_09017_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "gemm_tc*.cu")) + glob.glob(os.path.join(csrc, "gemm_tc_kernel.cuh")))
+    files += [os.path.join(csrc, f) for f in ("internal.cuh", "device_util.cuh", "tc_ptx.cuh")]
+    for f in files:
+        with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -263,6 +275,18 @@ def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, 
             "generate_s": gen_s, "plan_s": plan_s}
 
 
+def cpu_sample_input(w):
+    """Host input of the oracle's bounded sample for workload w: the whole matrix up to 8192 x 8192;
+    for larger workloads a stand-in with the workload's row count, CPU_PANEL_COLS columns and its
+    spectrum recipe (the full 32768 x 32768 matrix takes minutes to draw on the host)."""
+    from paper_2112_09017_gb300 import synth
+    if w.m * w.n <= 8192 * 8192:
+        return w.matrix(), f"the full {w.m}x{w.n} matrix"
+    a = synth.column_panel_stand_in(w.name, CPU_PANEL_COLS, w.seed)
+    return a, (f"a {a.shape[0]}x{a.shape[1]} host-drawn stand-in with the workload's row count and spectrum "
+               f"recipe (the full {w.m}x{w.n} matrix takes minutes to draw on the host)")
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, timed as it stands on the host cores."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -271,7 +295,7 @@ def run_reference(args):
         return 0
     from paper_2112_09017_gb300 import synth
     w = synth.WORKLOADS[args.workload]
-    a = w.matrix()
+    a, what = cpu_sample_input(w)
     for _ in range(args.warmup):
         cpu_oracle_sample(a, w.tol)
     tot_f, tot_t = 0.0, 0.0
@@ -282,7 +306,7 @@ def run_reference(args):
     value = tot_f / tot_t / 1e12
     cores = cpu_cores()
     sample = (f"oracle ns_polar (numpy float64) truncated to 1 Newton-Schulz update per step (2 Grams, 1 update, "
-              f"H) on the full {w.m}x{w.n} matrix; rate = algorithmic flops m n^2 (3k+3) / wall time")
+              f"H) on {what}; rate = algorithmic flops m n^2 (3k+3) / wall time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -372,6 +396,41 @@ def run_chebyshev(lib, torch, n, seed, stream, peaks, steps, warmup, world, degr
     return out
 
 
+def accuracy_sampled(torch, A, U, H, k=512, seed=0):
+    """orth and bwd in float64 from k sampled columns (large matrices): the rows S of U^T U - I,
+    and the columns S of A - U H, scaled to the full-matrix norms."""
+    n = U.shape[1]
+    S = torch.randperm(n, generator=torch.Generator(device="cuda").manual_seed(seed), device="cuda")[:k]
+    U64 = U.double()
+    rows = U64[:, S].T @ U64
+    rows[torch.arange(k, device="cuda"), S] -= 1.0
+    orth = math.sqrt(rows.square().sum().item() / k)
+    del rows
+    R = A[:, S].double() - U64 @ H[:, S].double()
+    bwd = math.sqrt(R.square().sum().item() / k * n) / torch.linalg.matrix_norm(A.double()).item()
+    return {"orth": orth, "bwd": bwd, "sampled_columns": k}
+
+
+def compact(x, digits=4):
+    """Floats rounded to `digits` significant digits (keeps the JSON line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: compact(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, digits) for v in x]
+    return x
+
+
+def device_input(synth, torch, w, rank):
+    """Workload w on the device: host recipe (numpy) up to 8192 x 8192, else drawn on the device
+    (synth.workload_on_device). Returns (A, a_np or None, closed-form U = Q1 Q2^T or None)."""
+    if w.m * w.n <= 8192 * 8192:
+        a_np, (q1, _, q2) = synth.matrix_with_spectrum(w.m, w.n, w.spectrum(), w.seed + rank, return_factors=True)
+        return torch.from_numpy(a_np).cuda(), a_np, torch.from_numpy(q1 @ q2.T).cuda()
+    return synth.workload_on_device(w.name, "cuda", seed_offset=rank), None, None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -383,14 +442,17 @@ def run_ours(args):
     lib = polar
     w = synth.WORKLOADS[args.workload]
     m, n = w.m, w.n
-    a_np, (q1, s, q2) = synth.matrix_with_spectrum(m, n, w.spectrum(), w.seed + rank, return_factors=True)
-    A = torch.from_numpy(a_np).cuda()
+    big = m * n > 8192 * 8192
+    t_gen = time.perf_counter()
+    A, a_np, q1q2t = device_input(synth, torch, w, rank)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_gen
     U = torch.empty((m, n), dtype=torch.float32, device="cuda")
     H = torch.empty((n, n), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     peaks, peak_src = load_peaks()
 
-    def timed(plan, steps, warmup, sampler=None):
+    def timed(plan, A, U, H, steps, warmup, sampler=None):
         for _ in range(warmup):
             plan(A, U=U, H=H)
         barrier(world)
@@ -410,15 +472,18 @@ def run_ours(args):
         ms = ev0.elapsed_time(ev1)
         return max_over_ranks(ms, world), infos, clocks
 
-    # ---- mixed / split precision (the chosen form) ----
+    # ---- mixed / split precision (the chosen form): the headline ----
     plan = lib.Plan(m, n, prec=args.prec, tol=w.tol, profile=1)
     sampler = ClockSampler(local)
-    ms, infos, clocks = timed(plan, args.steps, args.warmup, sampler)
+    ms, infos, clocks = timed(plan, A, U, H, args.steps, args.warmup, sampler)
     iters = infos[-1]["iters"]
     flops = sum(algorithmic_flops(m, n, i["iters"]) for i in infos)
     value = whole_job_rate(world, flops, ms) / 1e12
     solves_per_s = whole_job_rate(world, args.steps, ms)
-    acc = accuracy(torch, A, U, H, torch.from_numpy(q1 @ q2.T).cuda() if rank == 0 else None)
+    if big:
+        acc = accuracy_sampled(torch, A, U, H)
+    else:
+        acc = accuracy(torch, A, U, H, q1q2t if rank == 0 else None)
 
     # dominant kernel: the update product X <- 1.5 X - 0.5 X G (2/3 of the flops)
     P = {"bf16x6": 3, "bf16x3": 2, "bf16": 1, "fp32": 0}.get(args.prec, 3)
@@ -448,42 +513,44 @@ def run_ours(args):
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz", "launch_ms": avg_s * 1e3}
     launches = sum(i["launches"] for i in infos)
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- end to end through the C ABI with host buffers (polar_run_host: copies inside the call) ----
     A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
-    A_h.copy_(torch.from_numpy(a_np))
+    A_h.copy_(A.cpu() if a_np is None else torch.from_numpy(a_np))
     U_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
     H_h = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
-    A_d = torch.empty_like(A)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 2 if big else 3))
+    plan.run_host(A_h, U=U_h, H=H_h)          # first call allocates the plan's device copies
     barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     e2e_flops = 0.0
     for _ in range(e2e_steps):
-        A_d.copy_(A_h, non_blocking=True)
-        _, _, info = plan(A_d, U=U, H=H)
-        U_h.copy_(U, non_blocking=True)
-        H_h.copy_(H, non_blocking=True)
+        _, _, info = plan.run_host(A_h, U=U_h, H=H_h)
         e2e_flops += algorithmic_flops(m, n, info["iters"])
     ev1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     e2e = {"value": world * e2e_flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": (m * n + n * n) * 4,
-           "ms_per_step": e2e_ms / e2e_steps}
+           "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps,
+           "api": "polar_run_host: pinned host A, U, H; the H2D and D2H copies run inside the C-ABI call"}
     plan.close()
+    del A_h, U_h, H_h
 
-    # ---- the plain FP32 form on the same input ----
+    # ---- the plain FP32 form on the same input (one solve at the large size) ----
     plain = None
     if not args.no_plain and args.prec != "fp32":
         pplan = lib.Plan(m, n, prec="fp32", tol=w.tol)
-        pms, pinfos, _ = timed(pplan, max(1, min(args.steps, 3)), min(args.warmup, 3))
+        U2, H2 = torch.empty_like(U), torch.empty_like(H)
+        psteps, pwarm = (1, 0) if big else (max(1, min(args.steps, 3)), min(args.warmup, 3))
+        pms, pinfos, _ = timed(pplan, A, U2, H2, psteps, pwarm)
         pflops = sum(algorithmic_flops(m, n, i["iters"]) for i in pinfos)
-        pacc = accuracy(torch, A, U, H)
-        plain = {"value": world * pflops / (pms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                 "ms_per_step": pms / len(pinfos), "iters": pinfos[-1]["iters"], **pacc}
+        pacc = accuracy_sampled(torch, A, U2, H2) if big else accuracy(torch, A, U2, H2)
+        plain = {"value": world * pflops / (pms * 1e-3) / 1e12, "ms_per_step": pms / len(pinfos),
+                 "iters": pinfos[-1]["iters"], "orth": pacc["orth"], "bwd": pacc["bwd"]}
         pplan.close()
+        del U2, H2
 
     # ---- context: one Newton-Schulz step with cuBLAS FP32 products (TF32 off), per step ----
     cublas = None
@@ -496,90 +563,37 @@ def run_ours(args):
             G = X.T @ X
             return 1.5 * X - 0.5 * (X @ G)
 
-        for _ in range(2):
-            step()
+        step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2 if big else 3
         e0.record(stream)
-        for _ in range(3):
+        for _ in range(reps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
         torch.backends.cuda.matmul.allow_tf32 = prev
-        st_ms = e0.elapsed_time(e1) / 3
-        cublas = {"ms_per_ns_step": st_ms, "est_ms_per_solve": st_ms * (iters + 1),
-                  "note": "torch.matmul FP32 with TF32 off: full X^T X and X G per step (4 m n^2 flops), "
-                          "scaled by the solve's step count; context for the plain-FP32 comparison"}
+        cublas = e0.elapsed_time(e1) / reps * (iters + 1)
         del X
-
-    # ---- Algorithm 1 (preconditioned iteration) on the same input, beside the fixed form ----
-    pre = None
-    if not args.no_precond:
-        qplan = lib.Plan(m, n, prec=args.prec, tol=w.tol, precondition=1)
-        qms, qinfos, _ = timed(qplan, max(1, min(args.steps, 3)), min(args.warmup, 3))
-        qacc = accuracy(torch, A, U, H)
-        qplan.close()
-        qsteps = len(qinfos)
-        pre = {"ms_per_step": qms / qsteps, "solves_per_s": whole_job_rate(world, qsteps, qms),
-               "iters": qinfos[-1]["iters"], "n_precond": qinfos[-1]["n_precond"], **qacc,
-               "speedup_vs_fixed_form": (ms / args.steps) / (qms / qsteps)}
-
-    # ---- reduced-precision variants of the same solve, flagged against the 5e-6 bounds ----
-    variants = None
-    if not args.no_variants and args.prec == "bf16x6":
-        variants = {}
-        for vp in ("bf16x3", "bf16_then_x3", "bf16", "fp8_bf16_x3"):
-            vplan = lib.Plan(m, n, prec=vp, tol=w.tol)
-            vms, vinfos, _ = timed(vplan, max(1, min(args.steps, 2)), min(args.warmup, 2))
-            vacc = accuracy(torch, A, U, H)
-            vplan.close()
-            vit = vinfos[-1]["iters"]
-            variants[vp] = {"ms_per_step": vms / len(vinfos), "iters": vit,
-                            "status": "converged" if vinfos[-1]["status"] == lib.POLAR_OK else "not_converged",
-                            **vacc, "meets_5e-6": bool(vacc["orth"] <= 5e-6 and vacc["bwd"] <= 5e-6)}
-
-    # ---- Algorithm 2 (Newton-Schulz inverse) on a well-conditioned matrix of the same shape ----
-    inverse = None
-    if not args.no_inverse:
-        inverse = run_inverse(lib, torch, m, n, w.seed + 1000 + rank, stream, peaks, max(1, min(args.steps, 3)),
-                              min(args.warmup, 3), world)
-
-    # ---- Chebyshev matrix function (Clenshaw) on a symmetric matrix of the same size ----
-    cheb = None
-    if not args.no_chebyshev:
-        cheb = run_chebyshev(lib, torch, n, w.seed + 2000 + rank, stream, peaks, max(1, min(args.steps, 3)),
-                             min(args.warmup, 3), world)
-
-    # ---- batched configuration beside the single solve ----
-    batched = None
-    if args.batched > 0:
-        batched = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1)
-        peak_s = peaks.get("bf16_tflops_sustained")
-        batched["tensor_frac_of_measured_sustained"] = batched["split_tflops"] / peak_s if peak_s else None
-
-    # ---- small batched problems (n on [64, 128]): one SM each, against the grouped tile path ----
-    small = None
-    if args.batched > 0:
-        from paper_2112_09017_gb300 import synth
-        As = [synth.batched_problem_on_device(i, "cuda", 1e-3, 64, 128) for i in range(args.batched)]
-        on = run_batched(lib, torch, args.batched, max(1, min(args.steps, 3)), 2, 64, 128, onchip=1, As=As)
-        off = run_batched(lib, torch, args.batched, max(1, min(args.steps, 3)), 2, 64, 128, onchip=0, As=As)
-        peak_s = peaks.get("bf16_tflops_sustained")
-        small = {"onchip": on, "grouped": {k2: off[k2] for k2 in ("ms_per_batch", "solves_per_s", "value", "iters_p50")},
-                 "speedup_onchip_vs_grouped": off["ms_per_batch"] / on["ms_per_batch"],
-                 "onchip_tensor_frac_of_measured_sustained": (on["onchip_mma_tflops"] / peak_s)
-                 if (peak_s and on["onchip_mma_tflops"]) else None}
-        del As
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if not args.no_cpu and world == 1:
-        f, t, it = cpu_oracle_sample(a_np, w.tol, max_iter=1)
+        a_cpu, what = (a_np, f"the full {m}x{n} matrix") if a_np is not None else cpu_sample_input(w)
+        f, t, it = cpu_oracle_sample(a_cpu, w.tol, max_iter=1)
         cpu = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle ns_polar (numpy float64) on the full {m}x{n} matrix truncated to {it} update "
-                         f"({it + 1} Grams, {it} update, H): {t:.1f} s"}
+               "sample": f"oracle ns_polar (numpy float64) truncated to {it} update ({it + 1} Grams, {it} update, H) "
+                         f"on {what}: {t:.1f} s"}
+    del A, U, H
+    torch.cuda.empty_cache()
+
+    # ---- extra legs on the 8192 x 8192 workload (and the batched configurations) ----
+    legs = {} if args.no_legs else run_legs(args, lib, torch, synth, stream, peaks, world, rank)
 
     if rank == 0:
+        if legs:
+            sys.stderr.write("legs: " + json.dumps(compact(legs)) + "\n")
+            sys.stderr.flush()
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -589,29 +603,109 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": w.name, "m": m, "n": n, "kappa": w.kappa, "tol": w.tol, "precision": args.prec,
                        "l2": f"inputs larger than L2 (A is {m * n * 4 / 2**20:.0f} MiB; L2 129 MB)",
-                       "parallelism": "independent replicas" if world > 1 else "single GPU"},
-            "solves_per_s": solves_per_s, "iters": iters,
-            "paper_convention_tflops": value * (4.0 * iters) / (3 * iters + 3),
-            "accuracy": acc,
-            "kernel_ms": {"gram_avg": ms_gram / max(n_gram, 1), "update_avg": ms_upd / max(n_upd, 1),
-                          "n_gram": n_gram, "n_update": n_upd},
-            "plain_fp32": plain, "plain_fp32_cublas_context": cublas,
+                       "parallelism": "independent replicas" if world > 1 else "single GPU",
+                       "input": "drawn on the device: float32 QR factors, float64 product" if big else
+                                "host recipe (numpy float64)"},
+            "gpu_launches": launches, "solves_per_s": solves_per_s, "iters": iters,
+            "paper_convention_tflops": value * (4.0 * iters) / (3 * iters + 3), "accuracy": acc,
+            "kernel_ms": {"gram": ms_gram / max(n_gram, 1), "update": ms_upd / max(n_upd, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+            "legs": legs.get("summary"), "input_gen_s": gen_s,
+            "plain_fp32": plain, "cublas_fp32_est_ms": cublas,
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-            "batched": batched, "batched_small": small, "preconditioned": pre, "ns_inverse": inverse,
-            "chebyshev": cheb, "precision_variants": variants,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(compact(line)), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 
 
+def run_legs(args, lib, torch, synth, stream, peaks, world, rank):
+    """The measured legs beside the headline, on the 8192 x 8192 workload: the fixed form and
+    Algorithm 1, the reduced-precision variants, Algorithm 2, a Chebyshev function, and the
+    batched configurations. Returns {"summary": a few numbers for the JSON line, ...details}."""
+    lw = synth.WORKLOADS[LEGS_WORKLOAD]
+    m, n = lw.m, lw.n
+    A = synth.workload_on_device(lw.name, "cuda", seed_offset=rank)
+    U = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    H = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    steps, warm = max(1, min(args.steps, 3)), min(args.warmup, 3)
+
+    def solve_ms(plan, k, w0):
+        for _ in range(w0):
+            plan(A, U=U, H=H)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [plan(A, U=U, H=H)[2] for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), world) / k, infos[-1]
+
+    out, summary = {}, {}
+    fplan = lib.Plan(m, n, prec="bf16x6", tol=lw.tol, profile=1)
+    fms, finfo = solve_ms(fplan, steps, warm)
+    fplan.close()
+    facc = accuracy(torch, A, U, H)
+    ku = finfo["ms_update"] / max(finfo["n_update"], 1)
+    out["fixed_8192"] = {"ms_per_step": fms, "iters": finfo["iters"], **facc, "update_ms": ku,
+                         "update_tensor_frac": 6 * 2.0 * m * n * n / (ku * 1e-3) / 1e12 /
+                         peaks.get("bf16_tflops_sustained", 1.0)}
+    summary["fixed_8192_ms"] = fms
+    if not args.no_precond:
+        qplan = lib.Plan(m, n, prec="bf16x6", tol=lw.tol, precondition=1)
+        qms, qinfo = solve_ms(qplan, steps, warm)
+        qplan.close()
+        out["preconditioned_8192"] = {"ms_per_step": qms, "iters": qinfo["iters"], "n_precond": qinfo["n_precond"],
+                                      **accuracy(torch, A, U, H), "speedup_vs_fixed_form": fms / qms}
+        summary["precond_8192_ms"] = qms
+    if not args.no_variants:
+        variants = {}
+        for vp in ("bf16x3", "bf16_then_x3", "bf16", "fp8_bf16_x3"):
+            vplan = lib.Plan(m, n, prec=vp, tol=lw.tol)
+            vms, vinfo = solve_ms(vplan, max(1, min(args.steps, 2)), min(args.warmup, 2))
+            vplan.close()
+            vacc = accuracy(torch, A, U, H)
+            variants[vp] = {"ms_per_step": vms, "iters": vinfo["iters"],
+                            "status": "converged" if vinfo["status"] == lib.POLAR_OK else "not_converged",
+                            **vacc, "meets_5e-6": bool(vacc["orth"] <= 5e-6 and vacc["bwd"] <= 5e-6)}
+        out["precision_variants_8192"] = variants
+    del A, U, H
+    torch.cuda.empty_cache()
+    if not args.no_inverse:
+        out["ns_inverse"] = run_inverse(lib, torch, m, n, lw.seed + 1000 + rank, stream, peaks, steps, warm, world)
+        summary["inverse_tflops"] = out["ns_inverse"]["value"]
+    if not args.no_chebyshev:
+        out["chebyshev"] = run_chebyshev(lib, torch, n, lw.seed + 2000 + rank, stream, peaks, steps, warm, world)
+        summary["chebyshev_tflops"] = out["chebyshev"]["value"]
+    if args.batched > 0:
+        b = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1)
+        peak_s = peaks.get("bf16_tflops_sustained")
+        b["tensor_frac_of_measured_sustained"] = b["split_tflops"] / peak_s if peak_s else None
+        out["batched"] = b
+        summary["batched_solves_per_s"] = b["solves_per_s"]
+        summary["batched_split_frac"] = b["tensor_frac_of_measured_sustained"]
+        As = [synth.batched_problem_on_device(i, "cuda", 1e-3, 64, 128) for i in range(args.batched)]
+        on = run_batched(lib, torch, args.batched, steps, 2, 64, 128, onchip=1, As=As)
+        off = run_batched(lib, torch, args.batched, steps, 2, 64, 128, onchip=0, As=As)
+        out["batched_small"] = {"onchip": on,
+                                "grouped": {k2: off[k2] for k2 in ("ms_per_batch", "solves_per_s", "value",
+                                                                   "iters_p50")},
+                                "speedup_onchip_vs_grouped": off["ms_per_batch"] / on["ms_per_batch"],
+                                "onchip_tensor_frac_of_measured_sustained": (on["onchip_mma_tflops"] / peak_s)
+                                if (peak_s and on["onchip_mma_tflops"]) else None}
+        summary["small_onchip_solves_per_s"] = on["solves_per_s"]
+        del As
+    out["summary"] = summary
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -623,6 +717,7 @@ def main():
     ap.add_argument("--no-inverse", action="store_true", help="skip the Newton-Schulz inverse (Algorithm 2) leg")
     ap.add_argument("--no-chebyshev", action="store_true", help="skip the Chebyshev / Clenshaw leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the reduced-precision variants")
+    ap.add_argument("--no-legs", action="store_true", help="headline solve only (no 8192 or batched legs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

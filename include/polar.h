@@ -129,7 +129,9 @@ POLAR_API const char* polar_status_string(polar_status_t s);
 /* Create a plan for m x n problems (m >= n >= 1) and allocate its device workspace
  * on the current CUDA device. o may be NULL for defaults. The plan owns the workspace
  * until polar_plan_destroy. Errors: EINVAL (shape, prec), ENOMEM (allocation or
- * ws_limit), ENOTSUP (reserved prec), ECUDA. */
+ * ws_limit), ENOTSUP (reserved prec), ECUDA.
+ * Paper: Algorithm 1, "Require" (an M x N matrix with M >= N; real here) and Sec. III.D
+ * (the Frobenius scaling X_0 = A / ||A||_F the plan's first kernels compute). */
 POLAR_API polar_status_t polar_plan_create(polar_plan_t* plan, int64_t m, int64_t n, const polar_options_t* o);
 
 /* Bytes of device workspace the plan holds. */
@@ -146,34 +148,62 @@ POLAR_API polar_status_t polar_run(polar_plan_t plan, const float* A, int64_t ld
                          float* H, int64_t ldh, double tol, polar_info_t* info, polar_stream_t stream);
 
 /* Plan for `count` independent problems of sizes (m[i], n[i]) (host arrays), m[i] >= n[i] >= 1.
- * Problem i's matrices are packed row-major (ld = n[i]). */
+ * Problem i's matrices are packed row-major (ld = n[i]). Allocates every problem's workspace,
+ * builds the tile tables and captures the whole solve in a CUDA graph. Errors: EINVAL (count,
+ * sizes, prec), ENOTSUP (FP32, TF32X3 or the FP8 schedule), ENOMEM, ECUDA.
+ * Paper: Sec. III.D and Algorithm 1, applied to each problem on its own (the paper solves one
+ * matrix at a time; running many uneven problems through shared launches is this library's). */
 POLAR_API polar_status_t polar_batched_plan_create(polar_plan_t* plan, int count, const int64_t* m,
                                          const int64_t* n, const polar_options_t* o);
 
 /* Polar factorisation of every problem of a batched plan. A, U, H are HOST arrays of
- * `count` DEVICE pointers (A[i]: m_i x n_i, U[i]: m_i x n_i, H[i]: n_i x n_i, all packed).
- * iters_dev[i] (int32) and resid_dev[i] (float64) are device arrays receiving each
+ * `count` DEVICE pointers (A[i]: m_i x n_i, U[i]: m_i x n_i, H[i]: n_i x n_i, all packed);
+ * the arrays must hold exactly the plan's count and the matrices the plan's sizes (the
+ * library cannot check either: a short array or a smaller matrix is read or written out of
+ * bounds). iters_dev[i] (int32) and resid_dev[i] (float64) are device arrays receiving each
  * problem's update count and final residual; either may be NULL. Stream-asynchronous:
  * returns after enqueueing; per-problem status goes to the device arrays (a problem
- * that did not converge reports iters = -1 - updates). */
+ * that did not converge reports iters = -1 - updates; a device timeout INT32_MIN).
+ * Paper: Sec. III.D, Eq. NewtonSchulz and Algorithm 1 per problem (see the plan above). */
 POLAR_API polar_status_t polar_batched_run(polar_plan_t plan, const float* const* A, float* const* U,
                                  float* const* H, double tol, int32_t* iters_dev, double* resid_dev,
                                  polar_stream_t stream);
 
+/* polar_run with HOST buffers: A (m x n, lda >= n), U (m x n, ldu >= n) and H (n x n, ldh >= n) are
+ * host pointers (pinned memory gives full copy speed; pageable memory works). The plan copies A
+ * into device memory it owns (allocated on the first call, counted in its workspace and ws_limit),
+ * runs the solve of polar_run on `stream` and copies U and H back; it returns after U and H are in
+ * host memory. Same statuses as polar_run; U and H are written only for OK and NOT_CONVERGED.
+ * Paper: Sec. III.D, Eqs. NewtonSchulz and PolarDecomp, Algorithm 1. */
+POLAR_API polar_status_t polar_run_host(polar_plan_t plan, const float* A, int64_t lda, float* U, int64_t ldu,
+                                        float* H, int64_t ldh, double tol, polar_info_t* info,
+                                        polar_stream_t stream);
+
 POLAR_API void polar_plan_destroy(polar_plan_t plan);
 
+/* Device-side status of the stream-asynchronous products (polar_gemm, polar_syrk,
+ * polar_gemm_noalloc): waits for the work enqueued on `stream`, then reads and clears the
+ * current device's timeout word. Returns POLAR_ETIMEOUT when a tensor-core launch of one of
+ * those calls on this device had a bounded wait expire since the previous call (its C is then
+ * not fully written; the kernel returned on its own and the context stays usable), POLAR_ECUDA
+ * on a CUDA error or without an sm_103 device, else POLAR_OK. The word is shared by every
+ * stream of the device. The paper has no counterpart: error reporting of this library. */
+POLAR_API polar_status_t polar_async_status(polar_stream_t stream);
+
 /* C = alpha * op(A) op(B) + beta * C, op(X) = X or X^T (trans != 0), with op(A) M x K and
- * op(B) K x N, in precision `prec` (FP32, BF16, BF16X3, BF16X6). beta == 0 does not read C.
- * Stream-asynchronous. Split planes live in a library-owned per-device scratch buffer
- * that grows on demand (so this call may allocate). The building block of every step
- * of the iteration (Eq. NewtonSchulz is two such products). */
+ * op(B) K x N, in precision `prec` (FP32, BF16, BF16X3, BF16X6, AUTO: BF16X6 when min(M, N) >= 256,
+ * else FP32; the schedules return EINVAL). beta == 0 does not read C. Stream-asynchronous: a
+ * device-side timeout of the product is reported by polar_async_status. Split planes live in a
+ * library-owned per-device scratch buffer that grows on demand (so this call may allocate). The
+ * building block of every step of the iteration (Eq. NewtonSchulz is two such products). */
 POLAR_API polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
                           const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                           float* C, int64_t ldc, int prec, polar_stream_t stream);
 
 /* C = alpha * A^T A + beta * C for A k x n (lda >= n), C n x n (ldc >= n), storing the full
  * symmetric C (each off-diagonal pair computed once and mirrored). The Gram matrix
- * X^T X of Eq. NewtonSchulz. Stream-asynchronous; may allocate scratch as polar_gemm. */
+ * X^T X of Eq. NewtonSchulz. Stream-asynchronous (timeouts: polar_async_status); may allocate
+ * scratch as polar_gemm. */
 POLAR_API polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int64_t lda, float beta,
                           float* C, int64_t ldc, int prec, polar_stream_t stream);
 
@@ -243,10 +273,13 @@ POLAR_API polar_status_t polar_quantize_e4m3(const float* X, int64_t rows, int64
  * cannot take the synchronisation a cudaFree implies) use this variant, whose planes
  * live in one static device array of POLAR_NOALLOC_SCRATCH_BYTES per GPU, held from
  * the first use on that GPU until the process exits.
- * Arguments, layouts and results are those of polar_gemm. The BF16 modes need
- * prec_planes * (rows_A * round64(cols_A) + rows_B * round64(cols_B)) * 2 bytes of the
- * array (stored shapes, rows rounded as listed); a larger problem returns POLAR_ENOMEM
- * before any device work. FP32 needs no scratch. The first call on a device looks up the
+ * Arguments, layouts, precision resolution (AUTO included), device check, results and
+ * timeout reporting (polar_async_status) are those of polar_gemm. The BF16 modes need
+ * P * (round64(rows_A * round64(cols_A)) + round64(rows_B * round64(cols_B))) * 2 bytes of the
+ * array, P the mode's planes (3, 2, 1), rows and cols the stored shapes of A and B, round64
+ * rounding up to a multiple of 64: each row is padded to 64 elements and each plane to a multiple
+ * of 64 elements. A larger problem returns POLAR_ENOMEM before any device work. FP32 needs no
+ * scratch. The first call on a device looks up the
  * array's address there (cudaGetSymbolAddress with that device current), so make it
  * before any stream capture. All calls share the array and it keeps the last call's
  * contents: calls whose work overlaps on the GPU (other streams or threads) race. */

@@ -49,6 +49,17 @@ struct StopRule {
 };
 // Number of Eq. RogueScalar steps lifting s0 to s_minus (the first loop of Algorithm 1).
 int precond_steps(double s_minus, double s0);
+// Coefficients of update k, X_{k+1} = c1 X_k + c3 X_k G_k: a and -(4/27) a^3 for the preconditioning
+// steps of Algorithm 1 (Eq. RogueMatrix), 1.5 and -0.5 after them (Eq. NewtonSchulz); rounded to float32.
+__host__ __device__ inline void update_coeffs(const StopRule& rule, int k, float& c1, float& c3) {
+  if (k < rule.n_pre) {
+    c1 = (float)rule.pre_a;
+    c3 = (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a);
+  } else {
+    c1 = 1.5f;
+    c3 = -0.5f;
+  }
+}
 
 // Small batched problems solved on one SM each (onchip.cu): X_0's three planes at x0
 // (pitch ldp, plane stride xps, as the batched workspace stores them); the final
@@ -164,8 +175,13 @@ struct TcArgs {
                                                   // the launch does nothing while *planes_dyn <= 0
   int withhold_tma;                               // test hook: the producer issues no copies, so the
                                                   // bounded waits expire (set by the launcher)
+  unsigned int* err_out;                          // without st: word set to 1 when a bounded wait expired
+                                                  // (null: the device-wide word read by tc_take_error)
 };
 cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s);
+// Reads and clears the device-wide word that launches without st and err_out set on a
+// timeout; waits for `s` and writes the old value to *out.
+cudaError_t tc_take_error(cudaStream_t s, unsigned int* out);
 
 // Grouped launch: many independent problems in one persistent launch. Each problem
 // has an entry (its TMA maps and its own TcArgs: sizes, epilogue pointers, status);
@@ -194,8 +210,16 @@ struct TcGroupLaunch {
 cudaError_t launch_tc_gemm_grouped(const TcGroupLaunch& g, cudaStream_t s);
 // Fills entry->map_a / map_b for the operands of entry->args (host side).
 bool tc_make_entry_maps(TcGroupEntry* entry);
-int tc_gram_partials(int64_t n);
+// Residual partial slots a GRAM launch of an n x n triangle with `planes` planes writes (the CTA-pair
+// and single-CTA forms tile it differently), and the largest of the two (for allocation).
+int tc_gram_partials(int64_t n, int planes);
+int tc_gram_partials_max(int64_t n);
 bool tc_available();
+
+// Host helpers defined in polar_api.cu and shared with the other entry points.
+bool device_is_sm103(int* sms = nullptr);         // the current device is an sm_103 GPU
+int resolve_precision(int prec, int64_t n);       // POLAR_AUTO -> BF16X6 for n >= 256, FP32 below
+int product_planes(int prec);                     // BF16 planes of a product mode (0: FP32 or not a product mode)
 
 // ---------------------------------------------------------------------------------
 // Batched solves (batched.cu)

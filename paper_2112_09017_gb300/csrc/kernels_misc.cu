@@ -145,13 +145,12 @@ __global__ void residual_finalize_kernel(const double* __restrict__ partials, in
     } else {
       st->planes_next = rule.sched == 1 ? (r > rule.switch_residual ? 1 : 2) : rule.planes_fixed;
     }
-    if (k < rule.n_pre) {  // Eq. RogueMatrix: X <- a X - (4/27) a^3 X G
-      st->upd_c1 = (float)rule.pre_a;
-      st->upd_c3 = (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a);
-    } else {               // Eq. NewtonSchulz: X <- 1.5 X - 0.5 X G
-      st->upd_c1 = 1.5f;
-      st->upd_c3 = -0.5f;
-    }
+    // Eq. RogueMatrix (X <- a X - (4/27) a^3 X G) while preconditioning, then Eq. NewtonSchulz
+    // (X <- 1.5 X - 0.5 X G): the coefficients of update k
+    float c1, c3;
+    update_coeffs(rule, k, c1, c3);
+    st->upd_c1 = c1;
+    st->upd_c3 = c3;
   }
 }
 

@@ -27,10 +27,11 @@ namespace {
 
 static __device__ __align__(256) uint16_t g_noalloc_scratch[POLAR_NOALLOC_SCRATCH_BYTES / 2];
 
+// Per-device address of the array. Only a successful lookup is kept: a failed one
+// (its error cleared from the runtime's last-error slot) is retried by the next call.
 struct ScratchAddr {
-  std::once_flag once;
+  std::mutex mu;
   void* ptr = nullptr;
-  cudaError_t err = cudaSuccess;
 };
 ScratchAddr g_addr[64];
 
@@ -41,8 +42,15 @@ polar_status_t scratch_address(void** out) {
     return POLAR_ECUDA;
   }
   ScratchAddr& s = g_addr[dev];
-  std::call_once(s.once, [&s] { s.err = cudaGetSymbolAddress(&s.ptr, g_noalloc_scratch); });
-  if (s.err != cudaSuccess || !s.ptr) return POLAR_ECUDA;
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (!s.ptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return POLAR_ECUDA;
+    }
+    s.ptr = p;
+  }
   *out = s.ptr;
   return POLAR_OK;
 }
@@ -61,7 +69,10 @@ extern "C" polar_status_t polar_gemm_noalloc(int transA, int transB, int64_t M, 
   const int64_t a_rows = transA ? K : M, a_cols = transA ? M : K;
   const int64_t b_rows = transB ? N : K, b_cols = transB ? K : N;
   if (K > 0 && (lda < a_cols || ldb < b_cols)) return POLAR_EINVAL;
-  const int P = prec == POLAR_BF16X6 ? 3 : prec == POLAR_BF16X3 ? 2 : prec == POLAR_BF16 ? 1 : 0;
+  // the same device check and precision resolution as polar_gemm, in the same order
+  if (!device_is_sm103()) { cudaGetLastError(); return POLAR_ECUDA; }
+  prec = resolve_precision(prec, M < N ? M : N);
+  const int P = product_planes(prec);
   if (P == 0 && prec != POLAR_FP32) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (K == 0 || P == 0) {  // no scratch needed: the FP32 product reads its operands directly

@@ -89,6 +89,14 @@ polar_status_t scratch_get(size_t bytes, void** out) {
 
 }  // namespace
 
+namespace polar {
+bool device_is_sm103(int* sms) { return device_ok(sms); }
+int resolve_precision(int prec, int64_t n) { return prec == POLAR_AUTO ? (n >= 256 ? POLAR_BF16X6 : POLAR_FP32) : prec; }
+int product_planes(int prec) {
+  return prec == POLAR_BF16X6 ? 3 : prec == POLAR_BF16X3 ? 2 : prec == POLAR_BF16 ? 1 : 0;
+}
+}  // namespace polar
+
 struct polar_plan_s {
   bool batched = false;
   int64_t m = 0, n = 0;
@@ -99,6 +107,9 @@ struct polar_plan_s {
   // workspace
   std::vector<void*> allocs;
   size_t ws_bytes = 0;
+  float* hostA = nullptr;  // polar_run_host: device copies of A, U, H (allocated on first use)
+  float* hostU = nullptr;
+  float* hostH = nullptr;
   float* X[2] = {nullptr, nullptr};  // FP32 path: double buffer; BF16 path: X[0] in place
   int64_t ldx = 0;
   float* G = nullptr;  // FP32 Gram, and C = U^T A at the end (both paths)
@@ -192,10 +203,7 @@ void normalize_options(polar_options_t& o) {
   if (!(o.fp8_switch_residual > 0)) o.fp8_switch_residual = 0.5;
 }
 
-int resolve_prec(int prec, int64_t n) {
-  if (prec == POLAR_AUTO) return n >= 256 ? POLAR_BF16X6 : POLAR_FP32;
-  return prec;
-}
+int resolve_prec(int prec, int64_t n) { return polar::resolve_precision(prec, n); }
 
 polar_status_t plan_alloc(polar_plan_s* p, size_t bytes, void** out) {
   if (p->opt.ws_limit && p->ws_bytes + bytes > p->opt.ws_limit) return POLAR_ENOMEM;
@@ -277,7 +285,7 @@ polar_status_t plan_setup(polar_plan_s* p) {
   int np = frob_partials_blocks(m, n);
   np = std::max(np, simt_gram_tiles(n));
   np = std::max(np, 2 * symmetrize_blocks(n));
-  if (p->P) np = std::max(np, tc_gram_partials(n));
+  if (p->P) np = std::max(np, tc_gram_partials_max(n));
   p->nparts = np;
   if ((r = plan_alloc(p, (size_t)np * 8, &v)) != POLAR_OK) return r;
   p->partials = (double*)v;
@@ -415,7 +423,8 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
   p->launches += 2;
   // the finalize records the planes this Gram used (schedules: read on the device)
   // (the Gram epilogue stores the mirrored lower triangle itself)
-  return launch_residual_finalize(p->partials, tc_gram_partials(p->n), p->st, rule, k, rule.sched ? -1 : p->P, s);
+  return launch_residual_finalize(p->partials, tc_gram_partials(p->n, p->P), p->st, rule, k, rule.sched ? -1 : p->P,
+                                  s);
 }
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
@@ -542,7 +551,8 @@ polar_status_t run_single(polar_plan_s* p, const float* A, int64_t lda, float* U
     c.nplanes = p->P;
     c.epi = TC_EPI_STORE;
     c.C = p->G; c.ldc = p->ldg; c.alpha = 1.f; c.beta = 0.f;
-    c.st = nullptr;
+    c.st = nullptr;                  // the solve has stopped: the launch must run
+    c.err_out = &p->st->err_flags;   // a timeout still reaches this solve's status
     CK(launch_tc_gemm(c, s));
     p->launches += 3;
   }
@@ -643,6 +653,50 @@ polar_status_t polar_run(polar_plan_t plan, const float* A, int64_t lda, float* 
   return r;
 }
 
+polar_status_t polar_run_host(polar_plan_t plan, const float* A, int64_t lda, float* U, int64_t ldu, float* H,
+                              int64_t ldh, double tol, polar_info_t* info, polar_stream_t stream) {
+  if (!plan || plan->batched || !A || !U || !H) return POLAR_EINVAL;
+  const int64_t m = plan->m, n = plan->n;
+  if (lda < n || ldu < n || ldh < n) return POLAR_EINVAL;
+  size_t na = (size_t)((m - 1) * lda + n) * 4, nu = (size_t)((m - 1) * ldu + n) * 4,
+         nh = (size_t)((n - 1) * ldh + n) * 4;
+  if (overlaps(A, na, U, nu) || overlaps(A, na, H, nh) || overlaps(U, nu, H, nh)) return POLAR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!plan->hostA) {
+    void* v = nullptr;
+    polar_status_t r;
+    if ((r = plan_alloc(plan, (size_t)m * n * 4, &v)) != POLAR_OK) return r;
+    plan->hostA = (float*)v;
+    if ((r = plan_alloc(plan, (size_t)m * n * 4, &v)) != POLAR_OK) return r;
+    plan->hostU = (float*)v;
+    if ((r = plan_alloc(plan, (size_t)n * n * 4, &v)) != POLAR_OK) return r;
+    plan->hostH = (float*)v;
+  }
+  if (cudaMemcpy2DAsync(plan->hostA, (size_t)n * 4, A, (size_t)lda * 4, (size_t)n * 4, (size_t)m,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return POLAR_ECUDA;
+  }
+  polar_status_t r = run_single(plan, plan->hostA, n, plan->hostU, n, plan->hostH, n, tol, info, s);
+  if (r == POLAR_OK || r == POLAR_NOT_CONVERGED) {
+    if (cudaMemcpy2DAsync(U, (size_t)ldu * 4, plan->hostU, (size_t)n * 4, (size_t)n * 4, (size_t)m,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpy2DAsync(H, (size_t)ldh * 4, plan->hostH, (size_t)n * 4, (size_t)n * 4, (size_t)n,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      r = POLAR_ECUDA;
+  }
+  if (r == POLAR_ECUDA) cudaGetLastError();
+  return r;
+}
+
+polar_status_t polar_async_status(polar_stream_t stream) {
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  unsigned int v = 0;
+  if (tc_take_error((cudaStream_t)stream, &v) != cudaSuccess) { cudaGetLastError(); return POLAR_ECUDA; }
+  return v ? POLAR_ETIMEOUT : POLAR_OK;
+}
+
 polar_status_t polar_batched_plan_create(polar_plan_t* plan, int count, const int64_t* m, const int64_t* n,
                                          const polar_options_t* o) {
   if (!plan) return POLAR_EINVAL;
@@ -724,8 +778,8 @@ polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N, int64_t 
     g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
     return launch_simt_gemm(g, SIMT_EPI_STORE, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
   }
-  int P = planes_of(prec);
-  if (P == 0 || prec == POLAR_SCHED_BF16_THEN_X3) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  const int P = product_planes(prec);
+  if (P == 0) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
   if (!tc_available()) return POLAR_ENOTSUP;
   const int64_t lpa = round_up(a_cols, 64), lpb = round_up(b_cols, 64);
   const int64_t sa = round_up(a_rows * lpa, 64), sb = round_up(b_rows * lpb, 64);
@@ -766,8 +820,8 @@ polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int
     CK(launch_mirror_f32(C, ldc, n, nullptr, s));
     return POLAR_OK;
   }
-  int P = planes_of(prec);
-  if (P == 0 || prec == POLAR_SCHED_BF16_THEN_X3) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
+  const int P = product_planes(prec);
+  if (P == 0) return prec == POLAR_TF32X3 ? POLAR_ENOTSUP : POLAR_EINVAL;
   if (!tc_available()) return POLAR_ENOTSUP;
   const int64_t lp = round_up(n, 64);
   const int64_t sa = round_up(k * lp, 64);
@@ -853,6 +907,7 @@ extern "C" polar_status_t polar_ns_inverse(const float* A, int64_t rows, int64_t
     g.nplanes = P;
     g.epi = TC_EPI_STORE; g.triangular = 1;
     g.C = C; g.ldc = ldc; g.alpha = 1.f; g.beta = 0.f;
+    g.err_out = &st->err_flags;   // no skip test (st is not RUNNING yet), but a timeout is reported
     if (launch_tc_gemm(g, s) != cudaSuccess) break;
     if (launch_mirror_f32(C, ldc, M, nullptr, s) != cudaSuccess) break;
     if (launch_frob_partials(C, M, M, ldc, part, fb, s) != cudaSuccess) break;

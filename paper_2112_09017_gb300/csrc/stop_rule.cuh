@@ -30,8 +30,7 @@ __device__ __forceinline__ bool batched_step_rule(DevState& s, const StopRule& r
     s.status = ST_NOT_CONVERGED;
   else if (k >= rule.max_iter) s.status = ST_NOT_CONVERGED;
   else {
-    c1 = k < rule.n_pre ? (float)rule.pre_a : 1.5f;
-    c3 = k < rule.n_pre ? (float)(-(4.0 / 27.0) * rule.pre_a * rule.pre_a * rule.pre_a) : -0.5f;
+    update_coeffs(rule, k, c1, c3);
     s.upd_c1 = c1;
     s.upd_c3 = c3;
     return true;

@@ -74,6 +74,8 @@ def load():
         "polar_plan_create": (i32, [C.POINTER(vp), i64, i64, C.POINTER(polar_options_t)]),
         "polar_plan_workspace_bytes": (C.c_size_t, [vp]),
         "polar_run": (i32, [vp, vp, i64, vp, i64, vp, i64, f64, C.POINTER(polar_info_t), vp]),
+        "polar_run_host": (i32, [vp, vp, i64, vp, i64, vp, i64, f64, C.POINTER(polar_info_t), vp]),
+        "polar_async_status": (i32, [vp]),
         "polar_batched_plan_create": (i32, [C.POINTER(vp), i32, C.POINTER(i64), C.POINTER(i64),
                                             C.POINTER(polar_options_t)]),
         "polar_batched_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), f64, vp, vp, vp]),
@@ -163,15 +165,50 @@ def polar_run(plan, A, U, H, tol: float = 0.0, stream=None, raw_status: bool = F
     return d
 
 
-def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None):
+def polar_run_host(plan, A, U, H, tol: float = 0.0, stream=None, raw_status: bool = False):
+    """polar_run with host (CPU) float32 tensors A (m x n), U (m x n), H (n x n), row-major; pinned
+    memory copies fastest. The copies run inside the library call. Returns the info dict."""
+    for t, name in ((A, "A"), (U, "U"), (H, "H")):
+        if str(t.dtype) != "torch.float32" or t.dim() != 2 or t.is_cuda or t.stride(1) != 1:
+            raise ValueError(f"{name} must be a 2-D row-major float32 host tensor")
+    info = polar_info_t()
+    r = load().polar_run_host(plan, _ptr(A), A.stride(0), _ptr(U), U.stride(0), _ptr(H), H.stride(0), float(tol),
+                              C.byref(info), _stream(stream))
+    d = info.as_dict()
+    d["status"] = r
+    if not raw_status and r not in (POLAR_OK, POLAR_NOT_CONVERGED):
+        raise PolarError(r, "polar_run_host")
+    return d
+
+
+def polar_async_status(stream=None) -> int:
+    """Waits for `stream` and returns (and clears) the device's timeout status of the
+    stream-asynchronous products: POLAR_OK, POLAR_ETIMEOUT or POLAR_ECUDA."""
+    return load().polar_async_status(_stream(stream))
+
+
+class BatchedPlan:
+    """Handle of a batched plan that remembers the problem sizes it was made for, so that
+    polar_batched_run can check the tensors it is given (the C entry point takes neither a
+    count nor shapes). Passed to the library as the raw plan pointer."""
+
+    def __init__(self, handle, ms, ns):
+        self._as_parameter_ = handle
+        self.ms = tuple(int(x) for x in ms)
+        self.ns = tuple(int(x) for x in ns)
+
+
+def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None) -> BatchedPlan:
     cnt = len(ms)
+    if len(ns) != cnt:
+        raise ValueError("ms and ns must have the same length")
     am = (C.c_int64 * cnt)(*ms)
     an = (C.c_int64 * cnt)(*ns)
     h = C.c_void_p()
     r = load().polar_batched_plan_create(C.byref(h), cnt, am, an, C.byref(options) if options is not None else None)
     if r != POLAR_OK:
         raise PolarError(r, "polar_batched_plan_create")
-    return h
+    return BatchedPlan(h, ms, ns)
 
 
 def polar_batched_run(plan, As, Us, Hs, tol=0.0, iters_dev=None, resid_dev=None, stream=None):
@@ -179,13 +216,20 @@ def polar_batched_run(plan, As, Us, Hs, tol=0.0, iters_dev=None, resid_dev=None,
     packed row-major float32 CUDA tensors; iters_dev (int32) and resid_dev (float64) device
     arrays of at least len(As) entries, or None. Stream-asynchronous."""
     import torch
+    if not isinstance(plan, BatchedPlan):
+        raise TypeError("plan must be the BatchedPlan returned by polar_batched_plan_create")
     cnt = len(As)
+    if cnt != len(plan.ms):
+        raise ValueError(f"the plan holds {len(plan.ms)} problems, {cnt} were given")
     if len(Us) != cnt or len(Hs) != cnt:
         raise ValueError("As, Us and Hs must have the same length")
     for i, (a, u, h) in enumerate(zip(As, Us, Hs)):
         for t, name in ((a, "A"), (u, "U"), (h, "H")):
             if t.dtype != torch.float32 or t.dim() != 2 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError(f"{name}[{i}] must be a packed row-major 2-D float32 CUDA tensor")
+        if tuple(a.shape) != (plan.ms[i], plan.ns[i]):
+            raise ValueError(f"problem {i}: A has shape {tuple(a.shape)}, the plan was made for "
+                             f"{(plan.ms[i], plan.ns[i])}")
         if tuple(u.shape) != tuple(a.shape) or tuple(h.shape) != (a.shape[1], a.shape[1]):
             raise ValueError(f"problem {i}: U must be m x n and H n x n for A of shape {tuple(a.shape)}")
     for t, dt, name in ((iters_dev, torch.int32, "iters_dev"), (resid_dev, torch.float64, "resid_dev")):
@@ -339,6 +383,16 @@ class Plan:
             setattr(o, k, v)
         self.m, self.n = m, n
         self.handle = polar_plan_create(m, n, o)
+
+    def run_host(self, A, tol=0.0, U=None, H=None, stream=None, raw_status=False):
+        """The solve through polar_run_host: host tensors in and out (U, H pinned when not given)."""
+        import torch
+        if U is None:
+            U = torch.empty((self.m, self.n), dtype=torch.float32, pin_memory=True)
+        if H is None:
+            H = torch.empty((self.n, self.n), dtype=torch.float32, pin_memory=True)
+        info = polar_run_host(self.handle, A, U, H, tol, stream, raw_status)
+        return U, H, info
 
     def __call__(self, A, tol=0.0, U=None, H=None, stream=None, raw_status=False):
         import torch

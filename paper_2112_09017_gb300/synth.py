@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "haar_columns", "logspace_spectrum", "two_segment_spectrum", "matrix_with_spectrum",
     "Workload", "WORKLOADS", "make_workload", "batched_sizes", "batched_problem", "batched_problem_on_device",
-    "matrix_with_spectrum_on_device",
+    "matrix_with_spectrum_on_device", "workload_on_device", "column_panel_stand_in",
 ]
 
 
@@ -171,28 +171,66 @@ def batched_problem_on_device(i: int, device, sigma_min: float = 1e-3, n_lo: int
 
 
 def matrix_with_spectrum_on_device(m: int, n: int, sigma: np.ndarray, seed: int, device, qr_dtype=None,
-                                   return_factors: bool = False):
+                                   return_factors: bool = False, product_dtype=None):
     """A = fl32(Q1 diag(sigma) Q2^T) drawn on a CUDA device (large workloads whose
     host-side QR takes minutes): same recipe as ``matrix_with_spectrum`` with the
-    Gaussians from torch's generator seeded with `seed` and the QR and product in
-    `qr_dtype` (float64 by default) on the device."""
+    Gaussians from torch's generator seeded with `seed`, the QR in `qr_dtype` and the
+    product in `product_dtype` (both float64 by default) on the device.
+
+    A float32 QR is accurate enough for the spectrum: its factors are orthogonal to
+    about 1e-6, which moves every singular value of the product by that much
+    *relatively* (the perturbation is multiplicative). The product is what must run in
+    float64: a float32 product adds an absolute error of about 2^-24 ||A|| per entry,
+    which buries singular values far below 2^-24 (the 1e-8 end of the two-segment
+    spectrum) under rounding noise and changes the iteration count."""
     import torch
     qd = qr_dtype or torch.float64
+    pd = product_dtype or torch.float64
     g = torch.Generator(device=device).manual_seed(seed)
 
     def haar(rows, cols):
         q, r = torch.linalg.qr(torch.randn(rows, cols, device=device, generator=g, dtype=qd))
         d = torch.sign(torch.diagonal(r))
         d[d == 0] = 1.0
-        return q * d[None, :]
+        q.mul_(d[None, :])
+        del r
+        return q
 
     q1 = haar(m, n)
     q2 = haar(n, n)
-    s = torch.from_numpy(np.asarray(sigma, dtype=np.float64)).to(device=device, dtype=qd)
-    a = ((q1 * s[None, :]) @ q2.T).to(torch.float32).contiguous()
+    s = torch.from_numpy(np.asarray(sigma, dtype=np.float64)).to(device=device, dtype=pd)
+    if pd == qd:
+        a = ((q1 * s[None, :]) @ q2.T).to(torch.float32).contiguous()
+    else:
+        a = ((q1.to(pd) * s[None, :]) @ q2.to(pd).T).to(torch.float32).contiguous()
     if return_factors:
         return a, (q1, s, q2)
+    del q1, q2
     return a
+
+
+def workload_on_device(name: str, device, seed_offset: int = 0):
+    """The named single-solve workload drawn on a CUDA device: float64 QR and product
+    up to 32768 x 8192; for the 32768 x 32768 two-segment workload the QR runs in float32
+    (about 9 s per factor instead of about 100 s at this GPU's float64 rate) and the
+    product in float64 (about 64 s), which keeps the prescribed spectrum (see
+    ``matrix_with_spectrum_on_device``)."""
+    import torch
+    w = WORKLOADS[name]
+    qd = torch.float32 if w.m * w.n > 2 ** 28 else torch.float64
+    return matrix_with_spectrum_on_device(w.m, w.n, w.spectrum(), w.seed + seed_offset, device, qd,
+                                          product_dtype=torch.float64)
+
+
+def column_panel_stand_in(name: str, cols: int, seed: int = 0):
+    """A host-drawn stand-in for a bounded CPU sample of a large workload: the workload's
+    row count, `cols` columns and the workload's spectrum recipe over those columns
+    (log-spaced, or two-segment), drawn with the host recipe of ``matrix_with_spectrum``.
+    Its shape fixes the work of a sample, which is what a CPU rate is measured on."""
+    w = WORKLOADS[name]
+    c = min(cols, w.n)
+    sigma = two_segment_spectrum(c) if w.sigma_min == 0.0 else logspace_spectrum(c, w.sigma_min)
+    return matrix_with_spectrum(w.m, c, sigma, seed)
 
 
 def symmetric_with_spectrum_on_device(n: int, lam: np.ndarray, seed: int, device, return_factors: bool = False):

@@ -133,13 +133,40 @@ def test_binding_structs_match_the_header_layout(tmp_path):
 
 
 def test_batched_run_binding_rejects_bad_arguments():
-    """The batched binding checks its tensors before any call into the library."""
+    """The batched binding checks its tensors against the plan's count and sizes before any
+    call into the library (the C entry point takes neither, so a short pointer array or a
+    smaller matrix would be read or written out of bounds)."""
     torch = pytest.importorskip("torch")
     from paper_2112_09017_gb300 import polar
     a, h = torch.zeros(4, 3), torch.zeros(3, 3)
+    plan = polar.BatchedPlan(ctypes.c_void_p(), [4], [3])     # never passed to the library here
+    with pytest.raises(TypeError):
+        polar.polar_batched_run(None, [a], [a], [h])           # not a batched plan handle
     with pytest.raises(ValueError):
-        polar.polar_batched_run(None, [a], [a], [])            # lengths differ
+        polar.polar_batched_run(plan, [a], [a], [])            # lengths differ
     with pytest.raises(ValueError):
-        polar.polar_batched_run(None, [a], [a], [h])           # host tensors
+        polar.polar_batched_run(plan, [a], [a], [h])           # host tensors
     with pytest.raises(ValueError):
-        polar.polar_batched_run(None, [a.double()], [a], [h])  # not float32
+        polar.polar_batched_run(plan, [a.double()], [a], [h])  # not float32
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(plan, [a, a], [a, a], [h, h])  # more problems than the plan holds
+    two = polar.BatchedPlan(ctypes.c_void_p(), [4, 4], [3, 3])
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(two, [a], [a], [h])            # fewer problems than the plan holds
+    with pytest.raises(ValueError):
+        polar.polar_batched_run(polar.BatchedPlan(ctypes.c_void_p(), [5], [3]), [a], [a], [h])  # shape
+
+
+def test_new_entry_points_check_arguments_without_gpu(built_lib):
+    """polar_run_host rejects a missing plan on the host; polar_async_status reports the missing
+    device; the host-tensor binding rejects device-style arguments before any call."""
+    torch = pytest.importorskip("torch")
+    from paper_2112_09017_gb300 import polar
+    lib = polar.load()
+    assert lib.polar_run_host(None, None, 1, None, 1, None, 1, 0.0, None, None) == polar.POLAR_EINVAL
+    if not torch.cuda.is_available():
+        assert lib.polar_async_status(None) == polar.POLAR_ECUDA
+        assert lib.polar_gemm_noalloc(0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4,
+                                      polar.POLAR_AUTO, None) == polar.POLAR_EINVAL   # null C first
+    with pytest.raises(ValueError):
+        polar.polar_run_host(None, torch.zeros(4, 3, dtype=torch.float64), torch.zeros(4, 3), torch.zeros(3, 3))

@@ -116,7 +116,7 @@ def test_polar_bf16x6_matches_oracle(lib, torch_cuda, case):
     assert abs(info["iters"] - ref["iters_at"]) <= 1
     met = metrics(a, to_np(U), to_np(H), ref["U"])
     assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, met
-    assert met["fwd"] <= max(1e-7 * kappa, 1e-6), met
+    assert met["fwd"] <= 1e-7 * kappa, met
     assert info["sym_err"] <= 1e-5
     for k, (g, w) in enumerate(zip(info["res_hist"], ref["residuals"])):
         if w > 1e-3:
@@ -257,6 +257,51 @@ def test_full_size_tall32768x8192(lib, torch_cuda):
     assert fwd <= 1e-7 * w.kappa, fwd
 
 
+def test_full_size_square32768_k1e8(lib, torch_cuda):
+    """The large single solve at full size: 32768 x 32768 with the two-segment spectrum (kappa = 1e8),
+    drawn on the device (float32 QR factors, float64 product: the prescribed singular values to about
+    1e-6 relative). Iteration count against the spectrum's exact-arithmetic count, the residual
+    trajectory while the iteration is far from its last steps, sampled orth and bwd in float64, and
+    sampled entries of H against float64 dot products. The forward bound 1e-7 kappa = 10 exceeds the
+    largest possible ||U - U'||_F / sqrt(n) = 2, so it holds trivially at this kappa."""
+    torch = torch_cuda
+    w = synth.WORKLOADS["square32768_k1e8"]
+    A = synth.workload_on_device(w.name, "cuda")
+    n = w.n
+    U = torch.empty_like(A)
+    H = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    plan = lib.Plan(w.m, w.n, prec="bf16x6", tol=w.tol)
+    _, _, info = plan(A, U=U, H=H)
+    plan.close()
+    want = json.load(open(os.path.join(GOLDEN, "iteration_counts.json")))["workloads"][w.name]["iters"]
+    pred = scalar.predict_ns(w.spectrum(), w.tol)
+    assert pred["iters"] == want
+    assert info["status"] == lib.POLAR_OK and abs(info["iters"] - want) <= 1, info["iters"]
+    # float32 rounding of A moves the smallest singular values (about 1e-8 of ||A||_2) by up to a few
+    # parts in 1e3, which shows only in the last iterations' residuals
+    for k, (g, p) in enumerate(zip(info["res_hist"], pred["residuals"])):
+        if p > 0.1:
+            assert abs(g - p) <= 1e-2 * p, (k, g, p)
+    k = 512
+    S = torch.randperm(n, generator=torch.Generator(device="cuda").manual_seed(0), device="cuda")[:k]
+    U64 = U.double()
+    rows = U64[:, S].T @ U64
+    rows[torch.arange(k, device="cuda"), S] -= 1.0
+    orth = math.sqrt(rows.square().sum().item() / k)
+    del rows
+    R = A[:, S].double() - U64 @ H[:, S].double()
+    normA = torch.linalg.matrix_norm(A.double()).item()
+    bwd = math.sqrt(R.square().sum().item() / k * n) / normA
+    del R
+    assert orth <= 5e-6 and bwd <= 5e-6, (orth, bwd)
+    rng = np.random.default_rng(2)
+    ii = torch.from_numpy(rng.integers(0, n, 256)).cuda()
+    jj = torch.from_numpy(rng.integers(0, n, 256)).cuda()
+    A64 = A.double()
+    h_ij = 0.5 * ((U64[:, ii] * A64[:, jj]).sum(0) + (U64[:, jj] * A64[:, ii]).sum(0))
+    assert torch.max(torch.abs(H.double()[ii, jj] - h_ij)).item() <= 1e-5 * normA / math.sqrt(n)
+
+
 # ------------------------------------------------------------------ Algorithm 1 (preconditioned)
 
 from oracle.ns_polar import ns_polar_preconditioned  # noqa: E402
@@ -279,7 +324,7 @@ def test_polar_preconditioned_matches_oracle(lib, torch_cuda, prec, case):
     assert abs(info["iters"] - ref["iters_at"]) <= 1
     met = metrics(a, to_np(U), to_np(H), ref["U"])
     assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, met
-    assert met["fwd"] <= max(1e-7 * kappa, 1e-6), met
+    assert met["fwd"] <= 1e-7 * kappa, met
     # The coefficients of Eq. RogueMatrix are rounded to FP32 on the device (2^-24
     # relative) and the preconditioning map expands small singular values, so the
     # residuals move by ~1e-5 relative at r ~ 0.07 (a float64 run with only the

@@ -36,3 +36,35 @@ def test_bounded_wait_expires_and_context_survives(lib, monkeypatch):
     u = U.double()
     assert torch.linalg.matrix_norm(u.T @ u - torch.eye(200, dtype=torch.float64, device="cuda")).item() < 1e-4
     plan.close()
+
+
+def test_product_timeouts_reach_the_caller(lib, monkeypatch):
+    """The stream-asynchronous products (polar_gemm, polar_syrk, polar_gemm_noalloc) report an
+    expired bounded wait through polar_async_status; the next product on the same stream is
+    correct and the status is clear again."""
+    import torch
+    rng = np.random.default_rng(4)
+    a = torch.from_numpy(rng.standard_normal((300, 200)).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.standard_normal((200, 260)).astype(np.float32)).cuda()
+    exact = a.double() @ b.double()
+    gram = a.double().T @ a.double()
+    assert lib.polar_async_status() == lib.POLAR_OK
+    calls = [
+        ("polar_gemm", lambda c: lib.polar_gemm(a, b, c, prec=lib.POLAR_BF16X6), (300, 260), exact),
+        ("polar_gemm_noalloc", lambda c: lib.polar_gemm_noalloc(a, b, c, prec=lib.POLAR_BF16X6), (300, 260), exact),
+        ("polar_syrk", lambda c: lib.polar_syrk(a, c, prec=lib.POLAR_BF16X6), (200, 200), gram),
+    ]
+    for name, call, shape, want in calls:
+        c = torch.zeros(shape, device="cuda")
+        monkeypatch.setenv("POLAR_TEST_WITHHOLD_TMA", "1")
+        t0 = time.time()
+        call(c)                                   # enqueued: the call itself returns OK
+        st = lib.polar_async_status()
+        monkeypatch.delenv("POLAR_TEST_WITHHOLD_TMA")
+        assert st == lib.POLAR_ETIMEOUT, (name, st)
+        assert time.time() - t0 < 30.0
+        assert lib.polar_async_status() == lib.POLAR_OK      # read and cleared
+        call(c)
+        assert lib.polar_async_status() == lib.POLAR_OK, name
+        err = (c.double() - want).abs().max().item()
+        assert err <= 1e-4 * want.abs().max().item(), (name, err)

@@ -36,7 +36,10 @@ def _pair(lib, torch, shape, ta, tb, prec, seed):
     torch.cuda.synchronize()
     A64 = (a.T if ta else a).astype(np.float64)
     B64 = (b.T if tb else b).astype(np.float64)
-    planes = {lib.POLAR_BF16X6: 3, lib.POLAR_BF16X3: 2, lib.POLAR_BF16: 1}.get(prec)
+    eff = prec
+    if prec == lib.POLAR_AUTO:   # what both entry points resolve AUTO to
+        eff = lib.POLAR_BF16X6 if min(M, N) >= 256 else lib.POLAR_FP32
+    planes = {lib.POLAR_BF16X6: 3, lib.POLAR_BF16X3: 2, lib.POLAR_BF16: 1}.get(eff)
     bound = gemm_bound(np.abs(A64), np.abs(B64), K, np.abs(c0), 0.5, 2.0, planes)
     got_new, got_ref = to_np(C_new).astype(np.float64), to_np(C_ref).astype(np.float64)
     assert np.all(np.abs(got_new - got_ref) <= 2 * bound)
@@ -66,3 +69,33 @@ def test_noalloc_rejects_problems_above_the_array(lib, torch_cuda):
     assert 3 * 2 * n * n * 2 > NOALLOC_BYTES
     assert lib.polar_gemm_noalloc(A, A, C, False, False, 1.0, 0.0, lib.POLAR_BF16X6, raw_status=True) == \
         lib.POLAR_ENOMEM
+
+
+def test_noalloc_resolves_auto_like_polar_gemm(lib, torch_cuda):
+    """POLAR_AUTO picks BF16X6 at min(M, N) >= 256 and FP32 below, as polar_gemm does."""
+    torch = torch_cuda
+    _pair(lib, torch, (300, 280, 200), False, False, lib.POLAR_AUTO, 5)
+    _pair(lib, torch, (100, 300, 64), False, True, lib.POLAR_AUTO, 6)
+
+
+def test_noalloc_size_limit_is_exact(lib, torch_cuda):
+    """The documented bound P (round64(rows_A round64(cols_A)) + round64(rows_B round64(cols_B))) 2
+    bytes: 1664^3 in BF16X6 needs 33,226,752 bytes and runs; 1700^3 needs 35,251,200 and is refused."""
+    torch = torch_cuda
+
+    def need(n):
+        r64 = lambda x: (x + 63) // 64 * 64
+        return 3 * (r64(n * r64(n)) + r64(n * r64(n))) * 2
+
+    assert need(1664) <= NOALLOC_BYTES < need(1700)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(1664, 1664, device="cuda", generator=g)
+    B = torch.randn(1664, 1664, device="cuda", generator=g)
+    C_new = torch.zeros(1664, 1664, device="cuda")
+    C_ref = torch.zeros(1664, 1664, device="cuda")
+    assert lib.polar_gemm_noalloc(A, B, C_new, prec=lib.POLAR_BF16X6, raw_status=True) == lib.POLAR_OK
+    lib.polar_gemm(A, B, C_ref, prec=lib.POLAR_BF16X6)
+    torch.cuda.synchronize()
+    assert torch.equal(C_new, C_ref)   # same planes, same kernel: bit-identical
+    big = torch.zeros(1700, 1700, device="cuda")
+    assert lib.polar_gemm_noalloc(big, big, big.clone(), prec=lib.POLAR_BF16X6, raw_status=True) == lib.POLAR_ENOMEM
