@@ -217,7 +217,7 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, As=None):
+def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, As=None, tune=None):
     """The batched workload: `count` problems (n uniform on [n_lo, n_hi], m = n or 2n,
     sigma on [1e-3, 1]) in one polar_batched_run; solves/s and per-problem iterations.
     onchip = 0 sends the problems that fit one SM through the grouped tile kernels too."""
@@ -234,7 +234,7 @@ def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, 
     o.prec = lib.POLAR_BF16X6
     o.small_onchip = onchip
     t0 = time.perf_counter()
-    plan = lib.polar_batched_plan_create(ms, ns, o)
+    plan = lib.polar_batched_plan_create(ms, ns, o, tune=tune)
     plan_s = time.perf_counter() - t0
     it = torch.zeros(count, dtype=torch.int32, device="cuda")
     rs = torch.zeros(count, dtype=torch.float64, device="cuda")
@@ -263,6 +263,7 @@ def run_batched(lib, torch, count, steps, warmup, n_lo=64, n_hi=1024, onchip=1, 
     small = [(m, n, kk) for m, n, kk in zip(ms, ns, k) if onchip and n <= 128 and m <= 256]
     mma_small = sum(6.0 * 2 * 128 * (-(-n // 16) * 16) * (-(-m // 16) * 16) * (2 * kk + 1) for m, n, kk in small)
     return {"workload": f"batched{count}_n{n_lo}-{n_hi}_k1e3", "count": count, "ms_per_batch": ms_run,
+            "tuned": bool(tune),
             "small_onchip": onchip, "problems_on_chip": len(small),
             "onchip_mma_tflops": mma_small / (ms_run * 1e-3) / 1e12 if small else None,
             "solves_per_s": count / (ms_run * 1e-3), "value": flops / (ms_run * 1e-3) / 1e12, "unit": "TFLOP/s",
@@ -681,9 +682,21 @@ def run_legs(args, lib, torch, synth, stream, peaks, world, rank):
         out["chebyshev"] = run_chebyshev(lib, torch, n, lw.seed + 2000 + rank, stream, peaks, steps, warm, world)
         summary["chebyshev_tflops"] = out["chebyshev"]["value"]
     if args.batched > 0:
-        b = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1)
+        from paper_2112_09017_gb300 import autotune
         peak_s = peaks.get("bf16_tflops_sustained")
+        tune = autotune.load()
+        As = [synth.batched_problem_on_device(i, "cuda", 1e-3, 64, 1024) for i in range(args.batched)]
+        b = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1, As=As, tune=tune)
         b["tensor_frac_of_measured_sustained"] = b["split_tflops"] / peak_s if peak_s else None
+        if tune:
+            # which choice each bucket got, and the same batch with the library's defaults
+            b["tuning"] = [{"n": [e["n_lo"], e["n_hi"]], "m_over_n": "1" if e["aspect_hi"] <= 1.5 else "2",
+                            "tile_n": e["tile_n"], "slice_stages": e["slice_stages"]} for e in tune]
+            d = run_batched(lib, torch, args.batched, max(1, min(args.steps, 2)), 1, As=As)
+            b["default_ms_per_batch"] = d["ms_per_batch"]
+            b["speedup_tuned_vs_default"] = d["ms_per_batch"] / b["ms_per_batch"]
+            summary["batched_default_solves_per_s"] = d["solves_per_s"]
+        del As
         out["batched"] = b
         summary["batched_solves_per_s"] = b["solves_per_s"]
         summary["batched_split_frac"] = b["tensor_frac_of_measured_sustained"]

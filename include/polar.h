@@ -76,6 +76,18 @@ typedef enum {
 typedef void* polar_stream_t;
 typedef struct polar_plan_s* polar_plan_t;
 
+/* One entry of a batched plan's tuning table: the problems with n_lo <= n <= n_hi and
+ * aspect_lo <= m / n <= aspect_hi use the tile width and slice length given here (the first
+ * matching entry wins; problems no entry matches use the plan's options). Written by the
+ * library's autotuner (paper_2112_09017_gb300/autotune.py), which times the choices per size
+ * bucket and keeps the fastest whose orthogonality and backward errors stay within 5e-6. */
+typedef struct {
+  int64_t n_lo, n_hi;
+  double aspect_lo, aspect_hi;
+  int tile_n;        /* width of the grouped launches' output tiles: 128 or 256 (0: the plan's) */
+  int slice_stages;  /* 32-element k-stages accumulated per promoted slice, 1..8 (0: the library's) */
+} polar_tune_entry_t;
+
 typedef struct {
   double tol;              /* stop when ||X^T X - I||_F / sqrt(n) <= tol; <= 0 means 1e-6 */
   int max_iter;            /* maximum number of updates; <= 0 means 100 */
@@ -99,6 +111,9 @@ typedef struct {
                               problem with n <= 128 and m <= 256 in one CTA that keeps X, G and the
                               accumulators on its SM for the whole loop; 0 sends them through the
                               grouped tile kernels like the others */
+  const polar_tune_entry_t* tune; /* batched plans: a tuning table of n_tune entries (host memory, read
+                              only during plan creation), or NULL */
+  int n_tune;
 } polar_options_t;
 
 #define POLAR_HIST 128

@@ -250,11 +250,14 @@ struct BatchedPlan {
   TcGroupEntry* upd_e[2] = {nullptr, nullptr};
   TcGroupEntry* h2_e = nullptr;    // [count][2] candidates
   TcGroupEntry* h_e = nullptr;     // selected
-  TcTile* gram_t = nullptr;
-  TcTile* upd_t = nullptr;
-  TcTile* h_t = nullptr;
-  int64_t n_gram_t = 0, n_upd_t = 0, n_h_t = 0;
-  int tile_n = 256;                // width of the grouped launches' tiles (options.batched_tile_n)
+  // tile tables of the grouped Gram and update launches, one per tile width ([0]: 256, [1]: 128);
+  // each problem's width is its tuning entry's, else options.batched_tile_n
+  TcTile* gram_t[2] = {nullptr, nullptr};
+  TcTile* upd_t[2] = {nullptr, nullptr};
+  int64_t n_gram_t[2] = {0, 0}, n_upd_t[2] = {0, 0};
+  TcTile* h_t = nullptr;           // U^T A for H: 256-wide tiles for every problem
+  int64_t n_h_t = 0;
+  std::vector<int> tile_n_of, slice_of;   // per problem: tile width, k-stages per slice (0: default)
   OcTask* oc_tasks = nullptr;      // problems solved on one SM each (largest first)
   int n_oc = 0;
   int32_t* iters_scratch = nullptr;
@@ -329,36 +332,43 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
   BK_(cudaGetLastError());
   // the small problems' whole loops, one SM each; the grouped launches below skip them
   BK_(launch_onchip_ns(b->oc_tasks, b->n_oc, rule, &b->sh_d->tol, &b->sh_d->err, b->P, s));
-  // the grouped loop, unless every problem was solved on-chip
-  for (int k = 0; k <= b->opt.max_iter && b->n_gram_t > 0; ++k) {
-    TcGroupLaunch g{};
-    g.tile_n = b->tile_n;
-    g.nplanes = b->P;
-    g.epi = TC_EPI_GRAM; g.a_mn = 1; g.b_mn = 1;
-    g.tiles = b->gram_t; g.ntiles = b->n_gram_t; g.entries = b->gram_e[k & 1];
-    g.done = &b->sh_d->done;
-    g.err = &b->sh_d->err;
-    BK_(launch_tc_gemm_grouped(g, s));
+  // the grouped loop, unless every problem was solved on-chip; one launch per tile width in use
+  const int widths[2] = {256, 128};
+  for (int k = 0; k <= b->opt.max_iter && b->n_gram_t[0] + b->n_gram_t[1] > 0; ++k) {
+    for (int w = 0; w < 2; ++w) {
+      if (!b->n_gram_t[w]) continue;
+      TcGroupLaunch g{};
+      g.tile_n = widths[w];
+      g.nplanes = b->P;
+      g.epi = TC_EPI_GRAM; g.a_mn = 1; g.b_mn = 1;
+      g.tiles = b->gram_t[w]; g.ntiles = b->n_gram_t[w]; g.entries = b->gram_e[k & 1];
+      g.done = &b->sh_d->done;
+      g.err = &b->sh_d->err;
+      BK_(launch_tc_gemm_grouped(g, s));
+    }
     b_finalize_kernel<<<(count * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(b->meta_d, b->st_d, b->sh_d, count,
                                                                                    rule, k);
     BK_(cudaGetLastError());
     b_check_done_kernel<<<1, 1, 0, s>>>(b->sh_d, k);
     BK_(cudaGetLastError());
     if (k == b->opt.max_iter) break;
-    TcGroupLaunch u{};
-    u.tile_n = b->tile_n;
-    u.nplanes = b->P;
-    u.epi = TC_EPI_NS; u.a_mn = 0; u.b_mn = 1;
-    u.tiles = b->upd_t; u.ntiles = b->n_upd_t; u.entries = b->upd_e[k & 1];
-    u.done = &b->sh_d->done;
-    u.err = &b->sh_d->err;
-    BK_(launch_tc_gemm_grouped(u, s));
+    for (int w = 0; w < 2; ++w) {
+      if (!b->n_upd_t[w]) continue;
+      TcGroupLaunch u{};
+      u.tile_n = widths[w];
+      u.nplanes = b->P;
+      u.epi = TC_EPI_NS; u.a_mn = 0; u.b_mn = 1;
+      u.tiles = b->upd_t[w]; u.ntiles = b->n_upd_t[w]; u.entries = b->upd_e[k & 1];
+      u.done = &b->sh_d->done;
+      u.err = &b->sh_d->err;
+      BK_(launch_tc_gemm_grouped(u, s));
+    }
   }
   // H: C_p = U_p^T A_p for every problem, from the planes of its final iterate
   b_select_h_kernel<<<count, 64, 0, s>>>(b->h2_e, b->h_e, b->st_d, count);
   BK_(cudaGetLastError());
   TcGroupLaunch h{};
-  h.tile_n = b->tile_n;
+  h.tile_n = 256;
   h.nplanes = b->P;
   h.epi = TC_EPI_STORE; h.a_mn = 1; h.b_mn = 1;
   h.tiles = b->h_t; h.ntiles = b->n_h_t; h.entries = b->h_e;
@@ -385,9 +395,22 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   b->opt = opt;
   b->prec = prec;
   b->P = prec == POLAR_BF16X6 ? 3 : (prec == POLAR_BF16X3 || prec == POLAR_SCHED_BF16_THEN_X3) ? 2 : 1;
-  b->tile_n = opt.batched_tile_n == 128 ? 128 : 256;
   b->m.assign(m, m + count);
   b->n.assign(n, n + count);
+  // per-problem tile width and slice length: the first matching tuning entry, else the options
+  const int tile_default = opt.batched_tile_n == 128 ? 128 : 256;
+  b->tile_n_of.assign(count, tile_default);
+  b->slice_of.assign(count, 0);
+  for (int p = 0; p < count && opt.tune; ++p) {
+    const double aspect = (double)m[p] / (double)n[p];
+    for (int e = 0; e < opt.n_tune; ++e) {
+      const polar_tune_entry_t& te = opt.tune[e];
+      if (n[p] < te.n_lo || n[p] > te.n_hi || aspect < te.aspect_lo || aspect > te.aspect_hi) continue;
+      if (te.tile_n == 128 || te.tile_n == 256) b->tile_n_of[p] = te.tile_n;
+      if (te.slice_stages >= 1 && te.slice_stages <= 8) b->slice_of[p] = te.slice_stages;
+      break;
+    }
+  }
   polar_status_t r = POLAR_OK;
   void* v = nullptr;
   auto fail = [&](polar_status_t e) {
@@ -419,10 +442,14 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
   const bool oc_ok = opt.small_onchip != 0 && prec != POLAR_SCHED_BF16_THEN_X3;
   std::vector<int> order_tc, order_oc;
   for (int p : order) (oc_ok && onchip_fits(m[p], n[p]) ? order_oc : order_tc).push_back(p);
-  std::vector<TcTile> gram_t, upd_t, h_t;
-  build_tiles(order_tc, b->n, b->n, true, b->tile_n, gram_t, &ntg);
-  build_tiles(order_tc, b->m, b->n, false, b->tile_n, upd_t, nullptr);
-  build_tiles(order, b->n, b->n, false, b->tile_n, h_t, nullptr);
+  std::vector<int> order_w[2];
+  for (int p : order_tc) order_w[b->tile_n_of[p] == 256 ? 0 : 1].push_back(p);
+  std::vector<TcTile> gram_t[2], upd_t[2], h_t;
+  for (int w = 0; w < 2; ++w) {
+    build_tiles(order_w[w], b->n, b->n, true, w == 0 ? 256 : 128, gram_t[w], &ntg);
+    build_tiles(order_w[w], b->m, b->n, false, w == 0 ? 256 : 128, upd_t[w], nullptr);
+  }
+  build_tiles(order, b->n, b->n, false, 256, h_t, nullptr);
   size_t part_count = 0;
   for (int p = 0; p < count; ++p) part_count += (size_t)ntg[p] * kEpiWarps;
 
@@ -511,6 +538,7 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
       a.out_planes = mt.gp; a.ldo = mt.ldp; a.out_plane_stride = mt.gps; a.out_nplanes = kStored;
       a.partials = mt.partials;
       a.st = b->st_d + p;
+      a.slice_stages = b->slice_of[p];
       if (!tc_make_entry_maps(&g)) return fail(POLAR_ECUDA);
       TcGroupEntry& u = ue[p];
       memset(&u, 0, sizeof(u));
@@ -523,6 +551,7 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
       c.x_planes = mt.xp[par]; c.ldxp = mt.ldp; c.x_plane_stride = mt.xps;
       c.out_planes = mt.xp[par ^ 1]; c.ldo = mt.ldp; c.out_plane_stride = mt.xps; c.out_nplanes = kStored;
       c.st = b->st_d + p;
+      c.slice_stages = b->slice_of[p];
       if (!tc_make_entry_maps(&u)) return fail(POLAR_ECUDA);
       TcGroupEntry& h = he[2 * (size_t)p + par];
       memset(&h, 0, sizeof(h));
@@ -559,8 +588,10 @@ polar_status_t batched_create(BatchedPlan** out, int count, const int64_t* m, co
       return POLAR_ECUDA;
     return POLAR_OK;
   };
-  if ((r = put_tiles(gram_t, &b->gram_t, &b->n_gram_t)) != POLAR_OK) return fail(r);
-  if ((r = put_tiles(upd_t, &b->upd_t, &b->n_upd_t)) != POLAR_OK) return fail(r);
+  for (int w = 0; w < 2; ++w) {
+    if ((r = put_tiles(gram_t[w], &b->gram_t[w], &b->n_gram_t[w])) != POLAR_OK) return fail(r);
+    if ((r = put_tiles(upd_t[w], &b->upd_t[w], &b->n_upd_t[w])) != POLAR_OK) return fail(r);
+  }
   if ((r = put_tiles(h_t, &b->h_t, &b->n_h_t)) != POLAR_OK) return fail(r);
 
   // capture the whole sequence once; each run uploads its pointer tables and replays it

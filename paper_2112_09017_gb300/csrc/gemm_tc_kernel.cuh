@@ -258,6 +258,7 @@ struct TileCtx {
   int64_t bi, bj, nk;
   const TcArgs* args;
   int64_t part;  // partials slot base: tile index within its problem x EPI_WARPS
+  int sl;        // k-stages per promoted slice for this tile (its problem's, else the launch's)
 };
 
 // One problem: tiles enumerated by tile_coords (CG = 1), or pair tiles by pair_tile_coords, each CTA
@@ -285,6 +286,7 @@ struct SingleSrc {
     c.mb = mb;
     c.nk = nk;
     c.args = args;
+    c.sl = args->slice_stages > 0 ? args->slice_stages : 1;
     return true;
   }
 };
@@ -296,6 +298,7 @@ struct GroupSrc {
   const TcGroupEntry* entries;
   int64_t ntiles;
   int64_t t0, dt;
+  int sl_default;   // slice length of problems whose entry leaves it 0
   __device__ __forceinline__ bool get(int64_t t, TileCtx& c) const {
     const TcTile d = tiles[t];
     const TcGroupEntry* e = entries + d.prob;
@@ -306,6 +309,7 @@ struct GroupSrc {
     c.bj = d.bj;
     c.nk = (e->args.K + BK - 1) / BK;
     c.args = &e->args;
+    c.sl = e->args.slice_stages > 0 ? e->args.slice_stages : sl_default;
     c.part = (int64_t)d.local * EPI_WARPS;
     return true;
   }
@@ -397,7 +401,7 @@ __device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, ui
 
 template <int P, bool A_MN, bool B_MN, int TN, int CG, class Src>
 __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32_t tmem_base, Bars br,
-                                      volatile int* abort_flag, int SL, int pu) {
+                                      volatile int* abort_flag, int pu) {
   using C = Cfg<P, TN, CG>;
   constexpr int S = C::STAGES;
   const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * MN_CHUNK, 1024, 2)
@@ -420,9 +424,9 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
     uint32_t& buf_phase = gphase[grp];
     int kin = 0;  // k-stage index within the current slice
     for (int64_t kb = 0; kb < c.nk; ++kb) {
-      // SL k-stages into a fresh slice buffer, then published to the epilogue
+      // c.sl k-stages into a fresh slice buffer, then published to the epilogue
       const bool slice_start = kin == 0;
-      const bool slice_end = kin == SL - 1 || kb == c.nk - 1;
+      const bool slice_end = kin == c.sl - 1 || kb == c.nk - 1;
       const int bslot = 2 * grp + buf;
       if (slice_start && !mbar_wait(br.tempty0 + 8 * bslot, buf_phase ^ 1u, abort_flag)) { ok = false; break; }
       if (!mbar_wait(br.full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
@@ -456,7 +460,7 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
 
 template <int EPI, int TN, int CG, class Src>
 __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, Bars br, volatile int* abort_flag,
-                                           int SL, int warp, int lane) {
+                                           int warp, int lane) {
   const int q = warp & 3;                              // TMEM lane quarter this warp may access
   const int half = TN == BN ? (warp - 2) >> 2 : 0;     // TN = 256: which 128 of the tile's columns
   const int grp = TN == BN ? 0 : (warp - 2) >> 2;      // TN = 128: the group (alternate tiles)
@@ -471,7 +475,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     if (!src.get(t, ctx)) continue;
     if (TN != BN && (int)(ntile++ & 1) != grp) continue;   // the other group's tile
     const TcArgs& p = *ctx.args;
-    const int64_t nslices = (ctx.nk + SL - 1) / SL;
+    const int64_t nslices = (ctx.nk + ctx.sl - 1) / ctx.sl;
     constexpr bool NS = EPI == TC_EPI_NS || EPI == TC_EPI_NS_STEP;
     constexpr bool STEP = EPI == TC_EPI_NS_STEP;
     constexpr bool CLEN = EPI == TC_EPI_CLENSHAW;
@@ -679,7 +683,7 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
 
 // Shared prologue/epilogue of both launch forms; `Src` supplies the tiles.
 template <int P, bool A_MN, bool B_MN, int EPI, int TN, int CG, class Src>
-__device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, unsigned int* err_out, int SL,
+__device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_word, unsigned int* err_out,
                                         const int* planes_dyn, int withhold) {
   using C = Cfg<P, TN, CG>;
   constexpr int S = C::STAGES;
@@ -736,10 +740,10 @@ __device__ __forceinline__ void tc_body(const Src& src, DevState* st, int* err_w
   } else if (warp == 1) {
     if (lane == 0 && (CG == 1 || cluster_rank() == 0)) {   // a pair's MMAs come from its even CTA
       const int pu = planes_dyn ? min(max(*planes_dyn, 1), P) : P;
-      role_mma<P, A_MN, B_MN, TN, CG>(src, smem_base, tmem_base, br, abort_flag, SL, pu);
+      role_mma<P, A_MN, B_MN, TN, CG>(src, smem_base, tmem_base, br, abort_flag, pu);
     }
   } else {
-    role_epilogue<EPI, TN, CG>(src, tmem_base, br, abort_flag, SL, warp, lane);
+    role_epilogue<EPI, TN, CG>(src, tmem_base, br, abort_flag, warp, lane);
   }
 
   tc_fence_before();
@@ -785,8 +789,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   src.dt = gridDim.x;
   src.rank = 0;
   src.tri = p.triangular != 0;
-  tc_body<P, A_MN, B_MN, EPI, BN, 1>(src, p.st, nullptr, p.err_out, p.slice_stages > 0 ? p.slice_stages : 1,
-                                     p.planes_dyn, p.withhold_tma);
+  tc_body<P, A_MN, B_MN, EPI, BN, 1>(src, p.st, nullptr, p.err_out, p.planes_dyn, p.withhold_tma);
 }
 
 // CTA pairs: clusters of two; pair tiles t0 = cluster index, dt = number of clusters. Both CTAs read
@@ -809,8 +812,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
   src.dt = gridDim.x / 2;
   src.rank = cluster_rank();
   src.tri = p.triangular != 0;
-  tc_body<P, A_MN, B_MN, EPI, BN, 2>(src, p.st, nullptr, p.err_out, p.slice_stages > 0 ? p.slice_stages : 1,
-                                     p.planes_dyn, p.withhold_tma);
+  tc_body<P, A_MN, B_MN, EPI, BN, 2>(src, p.st, nullptr, p.err_out, p.planes_dyn, p.withhold_tma);
 }
 
 template <int P, bool A_MN, bool B_MN, int EPI, int TN>
@@ -822,8 +824,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_grouped_kernel(const __gr
   src.ntiles = g.ntiles;
   src.t0 = blockIdx.x;
   src.dt = gridDim.x;
-  tc_body<P, A_MN, B_MN, EPI, TN, 1>(src, nullptr, g.err, nullptr, g.slice_stages > 0 ? g.slice_stages : 1,
-                                     g.planes_dyn, g.withhold_tma);
+  src.sl_default = g.slice_stages > 0 ? g.slice_stages : 1;
+  tc_body<P, A_MN, B_MN, EPI, TN, 1>(src, nullptr, g.err, nullptr, g.planes_dyn, g.withhold_tma);
 }
 
 inline int sm_count() {

@@ -25,11 +25,17 @@ PREC = {"fp32": POLAR_FP32, "bf16x6": POLAR_BF16X6, "tf32x3": POLAR_TF32X3, "bf1
 PASSES = {0: 0, 1: 1, 2: 3, 3: 6}
 
 
+class polar_tune_entry_t(C.Structure):
+    _fields_ = [("n_lo", C.c_int64), ("n_hi", C.c_int64), ("aspect_lo", C.c_double), ("aspect_hi", C.c_double),
+                ("tile_n", C.c_int), ("slice_stages", C.c_int)]
+
+
 class polar_options_t(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec", C.c_int), ("stagnation", C.c_double),
                 ("stag_floor", C.c_double), ("switch_residual", C.c_double), ("ws_limit", C.c_size_t), ("profile", C.c_int),
                 ("precondition", C.c_int), ("s_minus", C.c_double), ("s0", C.c_double),
-                ("fp8_switch_residual", C.c_double), ("batched_tile_n", C.c_int), ("small_onchip", C.c_int)]
+                ("fp8_switch_residual", C.c_double), ("batched_tile_n", C.c_int), ("small_onchip", C.c_int),
+                ("tune", C.POINTER(polar_tune_entry_t)), ("n_tune", C.c_int)]
 
 
 class polar_info_t(C.Structure):
@@ -198,12 +204,29 @@ class BatchedPlan:
         self.ns = tuple(int(x) for x in ns)
 
 
-def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None) -> BatchedPlan:
+def tune_table(entries):
+    """A ctypes array of polar_tune_entry_t from dicts with keys n_lo, n_hi, aspect_lo, aspect_hi,
+    tile_n, slice_stages (the entries of an autotuner cache)."""
+    arr = (polar_tune_entry_t * len(entries))()
+    for i, e in enumerate(entries):
+        arr[i] = polar_tune_entry_t(int(e["n_lo"]), int(e["n_hi"]), float(e["aspect_lo"]), float(e["aspect_hi"]),
+                                    int(e.get("tile_n", 0)), int(e.get("slice_stages", 0)))
+    return arr
+
+
+def polar_batched_plan_create(ms, ns, options: polar_options_t | None = None, tune=None) -> BatchedPlan:
+    """A batched plan for problems of sizes (ms[i], ns[i]); `tune`: autotuner entries (dicts) or None."""
     cnt = len(ms)
     if len(ns) != cnt:
         raise ValueError("ms and ns must have the same length")
     am = (C.c_int64 * cnt)(*ms)
     an = (C.c_int64 * cnt)(*ns)
+    if tune:
+        if options is None:
+            options = polar_default_options()
+        table = tune_table(tune)           # kept alive until the call returns (the library copies it)
+        options.tune = C.cast(table, C.POINTER(polar_tune_entry_t))
+        options.n_tune = len(tune)
     h = C.c_void_p()
     r = load().polar_batched_plan_create(C.byref(h), cnt, am, an, C.byref(options) if options is not None else None)
     if r != POLAR_OK:
