@@ -145,6 +145,17 @@ __global__ void b_finalize_kernel(const BMeta* __restrict__ meta, DevState* __re
   }
 }
 
+// The lower triangle of every running problem's G planes from the upper one the grouped Gram
+// wrote. Grid (count, Y): block (p, y) takes problem p's 64 x 64 upper blocks y, y + Y, ...
+__global__ void b_mirror_kernel(const BMeta* __restrict__ meta, const DevState* __restrict__ st, const BShared* sh) {
+  if (sh->done) return;
+  const int p = blockIdx.x;
+  if (st[p].status != ST_RUNNING) return;
+  const BMeta& mt = meta[p];
+  __shared__ uint16_t tile[3 * 64 * 66];
+  mirror3_tiles(mt.gp, mt.ldp, mt.gps, mt.n, blockIdx.y, gridDim.y, tile);
+}
+
 __global__ void b_check_done_kernel(BShared* sh, int k) {
   if (sh->done) return;
   const int slot = k < POLAR_HIST + 8 ? k : POLAR_HIST + 7;
@@ -352,6 +363,8 @@ polar_status_t enqueue_all(BatchedPlan* b, cudaStream_t s) {
     b_check_done_kernel<<<1, 1, 0, s>>>(b->sh_d, k);
     BK_(cudaGetLastError());
     if (k == b->opt.max_iter) break;
+    b_mirror_kernel<<<dim3(count, 8), kThreads, 0, s>>>(b->meta_d, b->st_d, b->sh_d);
+    BK_(cudaGetLastError());
     for (int w = 0; w < 2; ++w) {
       if (!b->n_upd_t[w]) continue;
       TcGroupLaunch u{};

@@ -38,8 +38,8 @@
 //                 NS_STEP NS, plus float64 per-warp sums of (X_{k+1} - X_k)^2 and
 //                        X_{k+1}^2 (the step size of the inverse iteration)
 //                 PLANES the product itself as BF16 planes (an operand of the next product)
-//                 GRAM   BF16 planes of G (upper-triangle tiles, each entry
-//                        also stored at its mirror position) and float64
+//                 GRAM   BF16 planes of G's upper triangle (upper-triangle tiles;
+//                        a mirror pass fills the lower one) and float64
 //                        partials of ||G - I||_F^2 per tile and warp
 // Operands are K-major (stored MN x K, 64-byte swizzle, 32-element k-stages)
 // or MN-major (stored K x MN, 128-byte swizzle, 64-element MN chunks); three
@@ -532,10 +532,14 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       if (!row_ok || c0 >= p.N) continue;
       const bool full_chunk = c0 + 32 <= p.N;
       if (NS) {
-        // X_{k+1} = c1 X_k + c3 X_k G: X_k from its three planes (exact), result as planes
+        // X_{k+1} = c1 X_k + c3 X_k G: X_k from its three planes (exact), result as planes. A chunk
+        // that ends past column N still moves whole 32-value rows when the pitch holds them: the
+        // columns from N to the pitch are zero in X_k (the library zeroes its plane buffers and
+        // never writes a non-zero there), the product is zero there (the operand maps stop at N),
+        // so the padding stays zero and no element-by-element path is needed.
         const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
-        if (full_chunk) {
+        if (full_chunk || (c0 + 32 <= p.ldxp && c0 + 32 <= p.ldo)) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             uint4 h = *reinterpret_cast<const uint4*>(xr + 8 * i);
@@ -572,29 +576,35 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
           }
         }
       } else if (EPI == TC_EPI_GRAM) {
-        // planes of G for entries on and above the diagonal, mirrored below it
+        // planes of G for the chunks that reach the diagonal or lie above it, as whole 32-value rows;
+        // the strictly lower triangle is written afterwards by the mirror pass from the upper one
+        // (launch_mirror_planes3, or the batched solves' own), which also overwrites what a chunk
+        // crossing the diagonal stores below it. Columns past N hold zeros (the operand maps stop at N)
+        // and land in the pitch's padding, which no operand map reads.
+        if (c0 + 31 < r) continue;                 // entirely below the diagonal
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
-        uint16_t* pt = p.out_planes + c0 * p.ldo + r;
         float s_off = 0.f, s_diag = 0.f;
-        if (full_chunk && r < c0) {
+        if (r < c0) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
-          store_planes32_mirror(pr, pt, p.ldo, p.out_plane_stride, p.out_nplanes, v);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int64_t cc = c0 + j;
-            if (cc < p.N && r <= cc) {
-              if (r == cc) {
-                float d = v[j] - 1.0f;
-                s_diag = fmaf(d, d, s_diag);
-              } else {
-                s_off = fmaf(v[j], v[j], s_off);
-                store_planes1(pt + j * p.ldo, p.out_plane_stride, p.out_nplanes, v[j]);
-              }
-              store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
+            if (cc == r) {
+              float d = v[j] - 1.0f;
+              s_diag = fmaf(d, d, s_diag);
+            } else if (cc > r && cc < p.N) {
+              s_off = fmaf(v[j], v[j], s_off);
             }
           }
+        }
+        if (c0 + 32 <= p.ldo) {
+          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < p.N) store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
         }
         part += 2.0 * (double)s_off + (double)s_diag;
       } else if (CLEN) {
@@ -644,12 +654,26 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
         }
       } else {  // STORE
         float* cr = p.C + r * p.ldc + c0;
+        if (full_chunk && !(tri && r > c0) && (reinterpret_cast<uintptr_t>(cr) & 15u) == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (c0 + j < p.N && !(tri && r > c0 + j)) {
-            float o = p.alpha * v[j];
-            if (p.beta != 0.0f) o = fmaf(p.beta, cr[j], o);
-            cr[j] = o;
+          for (int i = 0; i < 8; ++i) {
+            float4 o = make_float4(p.alpha * v[4 * i], p.alpha * v[4 * i + 1], p.alpha * v[4 * i + 2],
+                                   p.alpha * v[4 * i + 3]);
+            if (p.beta != 0.0f) {
+              const float4 c = reinterpret_cast<const float4*>(cr)[i];
+              o = make_float4(fmaf(p.beta, c.x, o.x), fmaf(p.beta, c.y, o.y), fmaf(p.beta, c.z, o.z),
+                              fmaf(p.beta, c.w, o.w));
+            }
+            reinterpret_cast<float4*>(cr)[i] = o;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (c0 + j < p.N && !(tri && r > c0 + j)) {
+              float o = p.alpha * v[j];
+              if (p.beta != 0.0f) o = fmaf(p.beta, cr[j], o);
+              cr[j] = o;
+            }
           }
         }
       }

@@ -98,6 +98,10 @@ cudaError_t launch_sym_finalize(const double* partials, int blocks, DevState* st
 cudaError_t launch_mirror_f32(float* C, int64_t ldc, int64_t n, const DevState* st, cudaStream_t s);
 cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride, int nplanes, int64_t n,
                                  const DevState* st, const int* planes_dyn, cudaStream_t s);
+// The strictly lower triangle of an n x n symmetric matrix's three BF16 planes from its upper
+// triangle (after a Gram launch, which writes the upper one); skipped unless st is RUNNING.
+cudaError_t launch_mirror_planes3(uint16_t* P, int64_t ldp, int64_t plane_stride, int64_t n, const DevState* st,
+                                  cudaStream_t s);
 cudaError_t launch_copy2d(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t m, int64_t n,
                           cudaStream_t s);
 cudaError_t launch_split_flat(const float* x, int64_t count, int nplanes, uint16_t* out, cudaStream_t s);

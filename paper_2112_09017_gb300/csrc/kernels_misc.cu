@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "device_util.cuh"
 #include "internal.cuh"
 
 namespace polar {
@@ -236,6 +237,15 @@ __global__ void mirror_kernel(T* __restrict__ C, int64_t ldc, int64_t plane_stri
       }
     }
   }
+}
+
+// The lower triangle of G's three planes from its upper triangle (the Gram epilogue writes the
+// upper one); skipped once the solve has stopped.
+__global__ void mirror_planes3_kernel(uint16_t* __restrict__ P, int64_t ldp, int64_t ps, int64_t n,
+                                      const DevState* __restrict__ st) {
+  if (st && st->status != ST_RUNNING) return;
+  __shared__ uint16_t tile[3 * 64 * 66];
+  mirror3_tiles(P, ldp, ps, n, blockIdx.x, gridDim.x, tile);
 }
 
 // Three BF16 planes that came from an FP32 value sum back to it exactly:
@@ -499,6 +509,13 @@ cudaError_t launch_mirror_f32(float* C, int64_t ldc, int64_t n, const DevState* 
 cudaError_t launch_mirror_planes(uint16_t* P, int64_t ldp, int64_t plane_stride, int nplanes, int64_t n,
                                  const DevState* st, const int* planes_dyn, cudaStream_t s) {
   mirror_kernel<uint16_t><<<mirror_blocks(n), kThreads, 0, s>>>(P, ldp, plane_stride, nplanes, n, st, planes_dyn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_planes3(uint16_t* P, int64_t ldp, int64_t plane_stride, int64_t n, const DevState* st,
+                                  cudaStream_t s) {
+  const int64_t nt = (n + 63) / 64, ntri = nt * (nt + 1) / 2;
+  mirror_planes3_kernel<<<(unsigned)(ntri < 2048 ? ntri : 2048), kThreads, 0, s>>>(P, ldp, plane_stride, n, st);
   return cudaGetLastError();
 }
 

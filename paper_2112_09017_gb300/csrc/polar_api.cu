@@ -421,10 +421,12 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
   if (e != cudaSuccess) return e;
   if ((e = prof_end(p, pi, s)) != cudaSuccess) return e;
   p->launches += 2;
-  // the finalize records the planes this Gram used (schedules: read on the device)
-  // (the Gram epilogue stores the mirrored lower triangle itself)
-  return launch_residual_finalize(p->partials, tc_gram_partials(p->n, p->P), p->st, rule, k, rule.sched ? -1 : p->P,
-                                  s);
+  // the finalize records the planes this Gram used (schedules: read on the device); then the lower
+  // triangle of G's planes from the upper one the Gram epilogue wrote (skipped once stopped)
+  e = launch_residual_finalize(p->partials, tc_gram_partials(p->n, p->P), p->st, rule, k, rule.sched ? -1 : p->P, s);
+  if (e != cudaSuccess) return e;
+  p->launches += 1;
+  return launch_mirror_planes3(p->Gp, p->ldp, p->gps, p->n, p->st, s);
 }
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
