@@ -188,25 +188,8 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t (&w)[3]) {
   }
 }
 
-__device__ __forceinline__ void store_planes32(uint16_t* base, int64_t pstride, int np, const float* x) {
-  // x: 32 consecutive values; writes np planes, 64 bytes each, 16-byte aligned
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    uint32_t w[3][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t t[3];
-      split2(x[8 * v + 2 * i], x[8 * v + 2 * i + 1], t);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) w[q][i] = t[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      if (q < np) reinterpret_cast<uint4*>(base + q * pstride)[v] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-  }
-}
-
-// As store_planes32, and also the mirrored entries: value j goes to row (c0 + j),
+// The three-plane split of 32 consecutive values (np planes, 64 bytes each, 16-byte stores) and also the
+// mirrored entries: value j goes to row (c0 + j),
 // column r of every plane (lanes hold consecutive r, so each store is 64 contiguous bytes).
 __device__ __forceinline__ void store_planes32_mirror(uint16_t* base, uint16_t* tbase, int64_t ld, int64_t pstride,
                                                       int np, const float* x) {
@@ -229,6 +212,59 @@ __device__ __forceinline__ void store_planes32_mirror(uint16_t* base, uint16_t* 
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       if (q < np) reinterpret_cast<uint4*>(base + q * pstride)[v] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+}
+
+// 4 x 4 transpose of 32-bit words across the four lanes of an aligned lane quad (lane c = lane & 3):
+// lane c holds x[j] = M[c][j] before and x[i] = M[i][c] after (two exchange rounds).
+__device__ __forceinline__ void quad_transpose(uint32_t (&x)[4], int c) {
+  {
+    const bool hi = (c & 2) != 0;
+    const uint32_t s0 = hi ? x[0] : x[2], s1 = hi ? x[1] : x[3];
+    const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0, 2), r1 = __shfl_xor_sync(0xffffffffu, s1, 2);
+    if (hi) { x[0] = r0; x[1] = r1; } else { x[2] = r0; x[3] = r1; }
+  }
+  {
+    const bool odd = (c & 1) != 0;
+    const uint32_t s0 = odd ? x[0] : x[1], s1 = odd ? x[2] : x[3];
+    const uint32_t r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+    if (odd) { x[0] = r0; x[2] = r1; } else { x[1] = r0; x[3] = r1; }
+  }
+}
+
+// The three-plane split of 32 consecutive values with the lanes' rows exchanged first: each lane holds 32 values of its own row;
+// a lane quad (lanes 4g..4g+3) transposes its 16-byte quads so that store i of lane 4g + c writes
+// quad c of row 4g + i. Every store instruction then covers 8 rows x 64 contiguous bytes instead of
+// 32 rows x 16 bytes. base: plane 0 at row 4g (of the lane's quad), column c0 + 8c; mask bit i:
+// row 4g + i may be written. Every lane of the warp must call it (the exchange is warp-wide); the
+// values are split in place (x is left holding the last remainders). Each plane is the
+// round-to-nearest-even BF16 of what the previous planes left (cvt.rn.bf16x2.f32).
+__device__ __forceinline__ void store_planes32_t(uint16_t* base, int64_t ld, int64_t pstride, int np, float* x,
+                                                 int c, unsigned mask) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q >= np) break;
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      uint32_t h;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x[2 * k + 1]), "f"(x[2 * k]));
+      w[k] = h;
+      x[2 * k] = x[2 * k] - __uint_as_float(h << 16);
+      x[2 * k + 1] = x[2 * k + 1] - __uint_as_float(h & 0xffff0000u);
+    }
+    uint32_t o[4][4];   // o[i][wp]: word wp of quad c of row 4g + i
+#pragma unroll
+    for (int wp = 0; wp < 4; ++wp) {
+      uint32_t y[4] = {w[wp], w[4 + wp], w[8 + wp], w[12 + wp]};
+      quad_transpose(y, c);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i][wp] = y[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (mask & (1u << i))
+        *reinterpret_cast<uint4*>(base + q * pstride + i * ld) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
   }
 }
 
@@ -523,14 +559,20 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     const float c3 = (NS && p.st) ? p.st->upd_c3 : -0.5f;
     const int64_t r = ctx.bi * BM + row_in_tile;
     const bool row_ok = r < p.M;
+    const int lq = lane & 3;                      // this lane's place in its quad (store_planes32_t)
+    const int64_t r4 = r - lq;                    // the quad's first row
     double part = 0.0;
     float d2 = 0.f, x2 = 0.f;  // NS_STEP: sum (x' - x)^2 and sum x'^2 over this thread's row chunk
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int64_t c0 = ctx.bj * TN + half * 128 + c * 32;
       float* v = &acc[c * 32];
-      if (!row_ok || c0 >= p.N) continue;
+      if (c0 >= p.N) continue;                    // the same for every lane of the warp
       const bool full_chunk = c0 + 32 <= p.N;
+      // rows of this lane's quad that exist (store_planes32_t writes rows r4 .. r4 + 3)
+      unsigned rows4 = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) rows4 |= (r4 + i < p.M) ? (1u << i) : 0u;
       if (NS) {
         // X_{k+1} = c1 X_k + c3 X_k G: X_k from its three planes (exact), result as planes. A chunk
         // that ends past column N still moves whole 32-value rows when the pitch holds them: the
@@ -540,11 +582,15 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
         const uint16_t* xr = p.x_planes + r * p.ldxp + c0;
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
         if (full_chunk || (c0 + 32 <= p.ldxp && c0 + 32 <= p.ldo)) {
+          // every lane takes part (rows past M read zeros and are not stored)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            uint4 h = *reinterpret_cast<const uint4*>(xr + 8 * i);
-            uint4 m = *reinterpret_cast<const uint4*>(xr + p.x_plane_stride + 8 * i);
-            uint4 l = *reinterpret_cast<const uint4*>(xr + 2 * p.x_plane_stride + 8 * i);
+            uint4 h = make_uint4(0u, 0u, 0u, 0u), m = h, l = h;
+            if (row_ok) {
+              h = *reinterpret_cast<const uint4*>(xr + 8 * i);
+              m = *reinterpret_cast<const uint4*>(xr + p.x_plane_stride + 8 * i);
+              l = *reinterpret_cast<const uint4*>(xr + 2 * p.x_plane_stride + 8 * i);
+            }
             const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, mw[4] = {m.x, m.y, m.z, m.w}, lw[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -559,8 +605,9 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
               v[8 * i + e] = xn;
             }
           }
-          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
-        } else {
+          store_planes32_t(p.out_planes + r4 * p.ldo + c0 + 8 * lq, p.ldo, p.out_plane_stride, p.out_nplanes, v, lq,
+                           rows4);
+        } else if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             if (c0 + j < p.N) {
@@ -581,10 +628,11 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
         // (launch_mirror_planes3, or the batched solves' own), which also overwrites what a chunk
         // crossing the diagonal stores below it. Columns past N hold zeros (the operand maps stop at N)
         // and land in the pitch's padding, which no operand map reads.
-        if (c0 + 31 < r) continue;                 // entirely below the diagonal
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
         float s_off = 0.f, s_diag = 0.f;
-        if (r < c0) {
+        if (!row_ok || c0 + 31 < r) {
+          // a row past M, or a chunk entirely below the diagonal: no terms
+        } else if (r < c0) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) s_off = fmaf(v[j], v[j], s_off);
         } else {
@@ -600,14 +648,20 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
           }
         }
         if (c0 + 32 <= p.ldo) {
-          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
-        } else {
+          // rows of the quad whose chunk reaches the diagonal or lies above it
+          unsigned upper4 = 0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) upper4 |= (c0 + 31 >= r4 + i) ? (1u << i) : 0u;
+          store_planes32_t(p.out_planes + r4 * p.ldo + c0 + 8 * lq, p.ldo, p.out_plane_stride, p.out_nplanes, v, lq,
+                           rows4 & upper4);
+        } else if (row_ok && c0 + 31 >= r) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             if (c0 + j < p.N) store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
         }
         part += 2.0 * (double)s_off + (double)s_diag;
       } else if (CLEN) {
+        if (!row_ok) continue;
         // Clenshaw step on the upper triangle, mirrored: alpha acc + beta Z + diag I, Z from its three planes
         const uint16_t* zr = p.x_planes + r * p.ldxp + c0;
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
@@ -643,16 +697,19 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
           }
         }
       } else if (EPI == TC_EPI_PLANES) {
-        // the product itself as three BF16 planes (an operand of the next product)
+        // the product itself as three BF16 planes (an operand of the next product); columns past N
+        // hold zeros (the operand maps stop at N) and land in the pitch's padding
         uint16_t* pr = p.out_planes + r * p.ldo + c0;
-        if (full_chunk) {
-          store_planes32(pr, p.out_plane_stride, p.out_nplanes, v);
-        } else {
+        if (c0 + 32 <= p.ldo) {
+          store_planes32_t(p.out_planes + r4 * p.ldo + c0 + 8 * lq, p.ldo, p.out_plane_stride, p.out_nplanes, v, lq,
+                           rows4);
+        } else if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             if (c0 + j < p.N) store_planes1(pr + j, p.out_plane_stride, p.out_nplanes, v[j]);
         }
       } else {  // STORE
+        if (!row_ok) continue;
         float* cr = p.C + r * p.ldc + c0;
         if (full_chunk && !(tri && r > c0) && (reinterpret_cast<uintptr_t>(cr) & 15u) == 0) {
 #pragma unroll
