@@ -353,6 +353,42 @@ def run_inverse(lib, torch, m, n, seed, stream, peaks, steps, warmup, world, kap
     return out
 
 
+def run_fp8_product(lib, torch, n, seed, stream, peaks, steps, warmup, world):
+    """C = Q(A) Q(B) for n x n float32 matrices on the FP8 tensor cores (polar_gemm_fp8: both
+    operands rounded to E4M3 per 128 x 128 tile, then the kind::f8f6f4 product), whole call timed.
+    Algorithmic work per call: 2 n^3; the roofline peak is the measured bf16 burst times the
+    nominal FP8 : BF16 ratio of 2."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    A = torch.randn((n, n), generator=g, device="cuda")
+    B = torch.randn((n, n), generator=g, device="cuda")
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        lib.polar_gemm_fp8(A, B, C, stream=stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        lib.polar_gemm_fp8(A, B, C, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world) / steps
+    tf = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    peak = 2.0 * peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None
+    # a sampled check: the product follows the quantized operands, not the float32 ones
+    rows = torch.arange(0, n, n // 64, device="cuda")
+    exact = (A[rows].double() @ B.double())
+    rel = float((C[rows].double() - exact).norm() / exact.norm())
+    out = {"value": world * tf, "unit": "TFLOP/s", "ms_per_call": ms, "n": n, "fp8_tflops": tf,
+           "frac_of_fp8_peak": (tf / peak) if peak else None,
+           "peak": peak, "peak_source": "measured bf16 burst x 2 (nominal FP8 : BF16 ratio)",
+           "rel_err_vs_float32_product": rel,
+           "note": "whole call per step: both E4M3 quantizations (codes and per-tile exponents) and the product"}
+    del A, B, C
+    return out
+
+
 def run_chebyshev(lib, torch, n, seed, stream, peaks, steps, warmup, world, degree=32):
     """exp(A) by a degree-`degree` Chebyshev series (Clenshaw summation, degree - 1 products)
     for a symmetric n x n matrix with eigenvalues evenly spread over [-1, 1], drawn on the device.
@@ -678,6 +714,10 @@ def run_legs(args, lib, torch, synth, stream, peaks, world, rank):
     if not args.no_inverse:
         out["ns_inverse"] = run_inverse(lib, torch, m, n, lw.seed + 1000 + rank, stream, peaks, steps, warm, world)
         summary["inverse_tflops"] = out["ns_inverse"]["value"]
+    if not args.no_variants:
+        out["fp8_product_16384"] = run_fp8_product(lib, torch, 16384, lw.seed + 3000 + rank, stream, peaks,
+                                                   max(steps, 3), max(warm, 2), world)
+        summary["fp8_product_tflops"] = out["fp8_product_16384"]["value"]
     if not args.no_chebyshev:
         out["chebyshev"] = run_chebyshev(lib, torch, n, lw.seed + 2000 + rank, stream, peaks, steps, warm, world)
         summary["chebyshev_tflops"] = out["chebyshev"]["value"]

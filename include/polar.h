@@ -215,6 +215,21 @@ POLAR_API polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N
                           const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                           float* C, int64_t ldc, int prec, polar_stream_t stream);
 
+/* C = alpha * Q(op(A)) Q(op(B)) + beta * C on the FP8 tensor cores (tcgen05.mma.kind::f8f6f4), op(A) M x K and
+ * op(B) K x N as in polar_gemm. Q rounds every 128 x 128 tile of its operand (tiles counted from element
+ * (0, 0) of op(X)) to FP8 E4M3 with a power-of-two scale, exactly as polar_quantize_e4m3; the products of
+ * the codes accumulate in float32, one 128-element block of K at a time, and each block is multiplied by
+ * its two tiles' scales (exact) and added with round-to-nearest. beta == 0 does not read C. Stream-
+ * asynchronous (timeouts: polar_async_status); may allocate scratch as polar_gemm. Row-major device
+ * buffers, caller-owned; lda, ldb, ldc in elements. Returns POLAR_EINVAL for negative sizes, a null C,
+ * null operands with K > 0 or leading dimensions below the row lengths; POLAR_ENOTSUP without tcgen05
+ * FP8 support; POLAR_ENOMEM when the scratch cannot grow; POLAR_ECUDA on a CUDA error; M == 0 or
+ * N == 0 is a no-op and K == 0 gives C = beta * C. The operands of the FP8 phase of
+ * POLAR_SCHED_FP8_BF16_X3. The paper has no counterpart: FP8 schedules are this library's. */
+POLAR_API polar_status_t polar_gemm_fp8(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                                        const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                                        float* C, int64_t ldc, polar_stream_t stream);
+
 /* C = alpha * A^T A + beta * C for A k x n (lda >= n), C n x n (ldc >= n), storing the full
  * symmetric C (each off-diagonal pair computed once and mirrored). The Gram matrix
  * X^T X of Eq. NewtonSchulz. Stream-asynchronous (timeouts: polar_async_status); may allocate

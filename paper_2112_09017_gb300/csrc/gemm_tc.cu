@@ -59,6 +59,22 @@ bool make_map(CUtensorMap* map, const TcOperand& op, int nplanes, bool mn_major,
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map over one plane of FP8 E4M3 codes (columns = K, rows, one plane), K-major, 128-byte rows of
+// the box with the 128-byte swizzle (the layout of the FP8 kernel's stages).
+bool make_map_u8(CUtensorMap* map, const TcOperand& op, int mn_box) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)op.cols, (cuuint64_t)op.rows, 1};
+  const uint64_t plane = ((uint64_t)op.ld * (uint64_t)op.rows + 15) / 16 * 16;
+  cuuint64_t strides[2] = {(cuuint64_t)op.ld, (cuuint64_t)plane};
+  cuuint32_t box[3] = {128, (cuuint32_t)mn_box, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint16_t*>(op.planes), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 // Device address of g_tc_error on the current device (looked up once per device), the error word
@@ -186,6 +202,33 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
     case 2: return tc_dispatch_single2(ma, mb, a, tm, tn, ntiles, s);
     default: return tc_dispatch_single3(ma, mb, a, tm, tn, ntiles, s);
   }
+}
+
+cudaError_t launch_tc_gemm_fp8(const TcArgs& a_in, cudaStream_t s) {
+  TcArgs a = a_in;
+  a.slice_stages = 1;                 // one 128-K block per slice: its scale is applied at the promotion
+  a.withhold_tma = withhold_tma();
+  if (!a.st && !a.err_out) a.err_out = default_error_word();
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0 || !a.a_exp || !a.b_exp || a.lde_a < (a.K + 127) / 128 ||
+      a.lde_b < (a.K + 127) / 128)
+    return cudaErrorInvalidValue;
+  if (!a.a.kmajor || !a.b.kmajor) return cudaErrorInvalidValue;
+  const TcOperand* ops[2] = {&a.a, &a.b};
+  for (const TcOperand* o : ops)
+    if (!o->planes || !aligned(o->planes, 16) || o->ld % 16 || o->ld < o->cols) return cudaErrorInvalidValue;
+  if (a.epi != TC_EPI_STORE && a.epi != TC_EPI_GRAM && a.epi != TC_EPI_NS) return cudaErrorInvalidValue;
+  if (a.epi != TC_EPI_STORE) {
+    if (!a.out_planes || !aligned(a.out_planes, 16) || a.ldo % 8 || a.out_plane_stride % 8 || a.out_nplanes != 3)
+      return cudaErrorInvalidValue;
+  }
+  if (a.epi == TC_EPI_GRAM && (!a.partials || !a.triangular)) return cudaErrorInvalidValue;
+  if (a.epi == TC_EPI_NS && (!a.x_planes || !aligned(a.x_planes, 16) || a.ldxp % 8 || a.x_plane_stride % 8))
+    return cudaErrorInvalidValue;
+  if (a.triangular && a.M != a.N) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map_u8(&ma, a.a, BM) || !make_map_u8(&mb, a.b, BN)) return cudaErrorInvalidValue;
+  const int64_t tm = (a.M + BM - 1) / BM, tn = (a.N + BN - 1) / BN;
+  return tc_dispatch_fp8(ma, mb, a, tm, tn, a.triangular ? tri_tiles(tm, tn) : tm * tn, s);
 }
 
 }  // namespace polar

@@ -86,16 +86,20 @@ constexpr uint32_t TMEM_COLS = 512;        // two 128 x 256 FP32 slice accumulat
 // Tile width TN: 256 (one epilogue group of eight warps, two 256-column TMEM slice buffers)
 // or 128 (two epilogue groups of four warps taking alternate tiles, two 128-column slice
 // buffers each, so that one group's output step overlaps the next tile's MMAs).
-// CG = 2: CTA pairs; each CTA stages TN / 2 of the tile's B columns.
+// CG = 2: CTA pairs; each CTA stages TN / 2 of the tile's B columns. P = FP8 (below): one plane of
+// FP8 E4M3 codes, 128-element (128-byte) k-stages, K-major operands only.
+constexpr int FP8 = 8;
 template <int P, int TN = BN, int CG = 1>
 struct Cfg {
   static constexpr int TNL = TN / CG;                     // B columns staged by one CTA
-  static constexpr int STAGES = CG == 2 ? (P == 3 ? 4 : (P == 2 ? 6 : 12))
+  static constexpr int BKE = P == FP8 ? 128 : BK;         // elements of K per k-stage
+  static constexpr int STAGES = P == FP8 ? 4
+                              : CG == 2 ? (P == 3 ? 4 : (P == 2 ? 6 : 12))
                               : TN == BN ? (P == 3 ? 6 : (P == 2 ? 9 : 16)) * 16 / BK : (P == 3 ? 4 : (P == 2 ? 6 : 12));
   static constexpr int NBUF = TN == BN ? 2 : 4;          // TMEM slice buffers of TN columns
   static constexpr int GROUP_WARPS = TN == BN ? EPI_WARPS : EPI_WARPS / 2;
-  static constexpr uint32_t A_BYTES = P * A_PLANE;
-  static constexpr uint32_t B_BYTES = P * TNL * BK * 2;
+  static constexpr uint32_t A_BYTES = P == FP8 ? BM * 128 : P * A_PLANE;
+  static constexpr uint32_t B_BYTES = P == FP8 ? TNL * 128 : P * TNL * BK * 2;
   static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr uint32_t NBARS = 2 * STAGES + 2 * NBUF + 1;
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 + 8 * NBARS + 16;
@@ -106,6 +110,11 @@ struct Cfg {
 __host__ __device__ constexpr uint32_t make_idesc(bool a_mn, bool b_mn, int tn = BN, int m = BM) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
          ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// FP8: D = F32, A = B = E4M3 (format code 0), both K-major, M = 128, N = tn.
+__host__ __device__ constexpr uint32_t make_idesc_f8(int tn = BN) {
+  return (1u << 4) | ((uint32_t)(tn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 // Plane pairs of the split product in issue order for `np` planes: the smallest
@@ -386,7 +395,7 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
       const uint32_t fbx = CG == 2 ? mapa_shared(fb, 0) : fb;   // the barrier the copies complete on
       const uint32_t a_dst = smem_base + stage * C::STAGE_BYTES;
       const uint32_t b_dst = a_dst + C::A_BYTES;
-      const int k0 = (int)(kb * BK);
+      const int k0 = (int)(kb * C::BKE);
       if (A_MN) {
 #pragma unroll
         for (int cc = 0; cc < BM / 64; ++cc) {
@@ -418,6 +427,15 @@ __device__ __noinline__ void role_producer(const Src& src, uint32_t smem_base, B
 
 // The NP-plane passes on one k-stage: descriptors are the stage-0 bases plus
 // compile-time offsets (the start-address field is the low 14 bits, address / 16).
+// FP8: the stage's 128 K-elements as four K = 32 MMAs on E4M3 codes (32 bytes of every row each).
+template <int TN>
+__device__ __forceinline__ void issue_stage_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t first_acc) {
+  constexpr uint32_t idesc = make_idesc_f8(TN);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    tc_mma_f8(d_tmem, a_desc + ((kk * 32) >> 4), b_desc + ((kk * 32) >> 4), idesc, kk == 0 ? first_acc : 1u);
+}
+
 template <int P, bool A_MN, bool B_MN, int NP, int TN = BN, int CG = 1>
 __device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t first_acc) {
   constexpr uint32_t idesc = make_idesc(A_MN, B_MN, TN, BM * CG);
@@ -440,9 +458,12 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
                                       volatile int* abort_flag, int pu) {
   using C = Cfg<P, TN, CG>;
   constexpr int S = C::STAGES;
-  const uint64_t a_desc0 = A_MN ? smem_desc(smem_base, P * MN_CHUNK, 1024, 2)
+  // FP8 operands: K-major rows of 128 bytes, 128-byte swizzle, 8-row groups of 1024 bytes
+  const uint64_t a_desc0 = P == FP8 ? smem_desc(smem_base, 16, 1024, 2)
+                         : A_MN ? smem_desc(smem_base, P * MN_CHUNK, 1024, 2)
                                 : smem_desc(smem_base, 16, KM_SBO, KM_SWZ);
-  const uint64_t b_desc0 = B_MN ? smem_desc(smem_base + C::A_BYTES, P * MN_CHUNK, 1024, 2)
+  const uint64_t b_desc0 = P == FP8 ? smem_desc(smem_base + C::A_BYTES, 16, 1024, 2)
+                         : B_MN ? smem_desc(smem_base + C::A_BYTES, P * MN_CHUNK, 1024, 2)
                                 : smem_desc(smem_base + C::A_BYTES, 16, KM_SBO, KM_SWZ);
   int stage = 0;
   uint32_t phase = 0;
@@ -470,10 +491,14 @@ __device__ __noinline__ void role_mma(const Src& src, uint32_t smem_base, uint32
       const uint32_t d_tmem = tmem_base + (uint32_t)(bslot * TN);
       const uint64_t soff = (uint64_t)((stage * C::STAGE_BYTES) >> 4);
       const uint32_t first_acc = slice_start ? 0u : 1u;
-      if (pu == P) issue_stage<P, A_MN, B_MN, P, TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
-      else if (pu == 2)
-        issue_stage<P, A_MN, B_MN, (P >= 2 ? 2 : P), TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
-      else issue_stage<P, A_MN, B_MN, 1, TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      if constexpr (P == FP8) {
+        issue_stage_f8<TN>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      } else {
+        if (pu == P) issue_stage<P, A_MN, B_MN, P, TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+        else if (pu == 2)
+          issue_stage<P, A_MN, B_MN, (P >= 2 ? 2 : P), TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+        else issue_stage<P, A_MN, B_MN, 1, TN, CG>(d_tmem, a_desc0 + soff, b_desc0 + soff, first_acc);
+      }
       // the stage is free in both CTAs of a pair, the slice is ready in both CTAs' TMEM
       if (CG == 2) tc_commit_pair(br.empty0 + 8 * stage, 3);
       else tc_commit(br.empty0 + 8 * stage);
@@ -518,16 +543,36 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
     float acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+    int e_sum = 0;
     bool ok = true;
     for (int64_t sl = 0; sl < nslices; ++sl) {
       const int bslot = 2 * grp + buf;
       if (!mbar_wait(br.tfull0 + 8 * bslot, buf_phase, abort_flag)) { ok = false; break; }
       tc_fence_after();
+      if (p.a_exp) {
+        // FP8 operands: the slice is one 128-K block, scaled by its tiles' powers of two (exact). Lane
+        // l holds the exponent sum of slice 32 j + l, fetched once per 32 slices; a half tile past N
+        // has no exponent (its columns are not stored).
+        if ((sl & 31) == 0) {
+          const int64_t bcol = ctx.bj * (TN / 128) + half, s2 = sl + lane;
+          e_sum = (s2 < nslices && bcol * 128 < p.N)
+                      ? (int)p.a_exp[ctx.bi * p.lde_a + s2] + (int)p.b_exp[bcol * p.lde_b + s2]
+                      : 0;
+        }
+        const float sc = ldexpf(1.0f, __shfl_sync(0xffffffffu, e_sum, (int)(sl & 31)));
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        float v[16];
-        tmem_ld16(t_lane + (uint32_t)(bslot * TN + c * 16), v);
-        add16_packed(&acc[c * 16], v);   // round-to-nearest promotion
+        for (int c = 0; c < 8; ++c) {
+          float v[16];
+          tmem_ld16(t_lane + (uint32_t)(bslot * TN + c * 16), v);
+          fma16_packed(&acc[c * 16], v, sc);   // round-to-nearest promotion of the scaled slice
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float v[16];
+          tmem_ld16(t_lane + (uint32_t)(bslot * TN + c * 16), v);
+          add16_packed(&acc[c * 16], v);   // round-to-nearest promotion
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -865,7 +910,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   src.tm = tm;
   src.tn = tn;
   src.ntiles = ntiles;
-  src.nk = (p.K + BK - 1) / BK;
+  src.nk = (p.K + Cfg<P>::BKE - 1) / Cfg<P>::BKE;
   src.t0 = blockIdx.x;
   src.dt = gridDim.x;
   src.rank = 0;
@@ -1056,6 +1101,8 @@ cudaError_t tc_dispatch_single3(const CUtensorMap& ma, const CUtensorMap& mb, co
                                 int64_t ntiles, cudaStream_t s);
 cudaError_t tc_dispatch_pair3(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int64_t tm2, int64_t tn,
                               int64_t ntiles, cudaStream_t s);
+cudaError_t tc_dispatch_fp8(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int64_t tm, int64_t tn,
+                            int64_t ntiles, cudaStream_t s);
 cudaError_t tc_dispatch_grouped1(const TcGroupLaunch& g, cudaStream_t s);
 cudaError_t tc_dispatch_grouped2(const TcGroupLaunch& g, cudaStream_t s);
 cudaError_t tc_dispatch_grouped3(const TcGroupLaunch& g, cudaStream_t s);

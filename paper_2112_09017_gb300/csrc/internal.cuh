@@ -120,6 +120,12 @@ cudaError_t launch_planes_to_f32(const uint16_t* planes, int64_t ldp, int64_t pl
 // three planes of an iterate (pitch ldp, plane stride sps); skipped unless st->fp8_on.
 cudaError_t launch_quantize_e4m3_planes(const uint16_t* src, int64_t ldp, int64_t sps, int64_t rows, int64_t cols,
                                         uint16_t* dst, int64_t ldd, const DevState* st, cudaStream_t s);
+// FP8 operands for the E4M3 tensor-core products: the E4M3 codes of every 128 x 128 tile of src (float32, or
+// three BF16 planes with from_planes) divided by that tile's power of two, and the exponents, optionally
+// transposed (codes and exponent table both); skipped unless st is null or RUNNING in its FP8 phase.
+cudaError_t launch_quantize_codes(const void* src, bool from_planes, int64_t lds, int64_t sps, int64_t rows,
+                                  int64_t cols, uint8_t* codes, int64_t ldc, int8_t* exps, int64_t lde, bool transpose,
+                                  const DevState* st, cudaStream_t s);
 // The same from a float32 matrix into a float32 matrix (library service).
 cudaError_t launch_quantize_e4m3_f32(const float* src, int64_t lds, int64_t rows, int64_t cols, float* dst,
                                      int64_t ldd, cudaStream_t s);
@@ -179,10 +185,18 @@ struct TcArgs {
                                                   // the launch does nothing while *planes_dyn <= 0
   int withhold_tma;                               // test hook: the producer issues no copies, so the
                                                   // bounded waits expire (set by the launcher)
+  const int8_t* a_exp;                            // FP8 operands: power-of-two exponents of A's 128 x 128 tiles,
+  const int8_t* b_exp;                            // a_exp[M block * lde_a + K block], b_exp[N block * lde_b +
+  int64_t lde_a, lde_b;                           // K block]; each 128-K slice is promoted times 2^(ea + eb)
   unsigned int* err_out;                          // without st: word set to 1 when a bounded wait expired
                                                   // (null: the device-wide word read by tc_take_error)
 };
 cudaError_t launch_tc_gemm(const TcArgs& a, cudaStream_t s);
+// The same on FP8 E4M3 codes (one byte per element; a.a and a.b K-major with plane_stride unused,
+// ld in bytes a multiple of 16) with a.a_exp, a.b_exp giving every 128 x 128 tile's power-of-two
+// scale: tcgen05.mma.kind::f8f6f4, one 128-K slice per promotion, each scaled exactly. Epilogues
+// STORE, GRAM and NS.
+cudaError_t launch_tc_gemm_fp8(const TcArgs& a, cudaStream_t s);
 // Reads and clears the device-wide word that launches without st and err_out set on a
 // timeout; waits for `s` and writes the old value to *out.
 cudaError_t tc_take_error(cudaStream_t s, unsigned int* out);

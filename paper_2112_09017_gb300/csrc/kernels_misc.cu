@@ -542,6 +542,180 @@ cudaError_t launch_cheb_affine_split(const float* A, int64_t lda, int64_t n, dou
   return cudaGetLastError();
 }
 
+// FP8 operands of the E4M3 tensor-core products: per 128 x 128 tile of src (rows x cols; float32, or
+// three BF16 planes summed), the exponent t of quantize_e4m3_kernel (the smallest power of two 2^t with
+// max|x| <= 448 2^t, 0 for a zero tile) and the E4M3 codes of x / 2^t (round to nearest even,
+// saturating). Codes go to codes[r * ldc + c], or transposed to codes[c * ldc + r]; t to
+// exps[tile_r * lde + tile_c], or transposed to exps[tile_c * lde + tile_r]. Skipped while st is not
+// RUNNING or its FP8 phase is over.
+//
+// Each thread takes four 4 x 4 blocks of the tile (rows 4 rb .. 4 rb + 3, rb = warp + 8 k; columns
+// 4 lane .. 4 lane + 3), so every load instruction of a warp reads 128 consecutive values of one row.
+// Codes are packed four to a word: as they are for the row-major output; for the transposed output
+// each 4 x 4 block of codes is transposed in registers and its four column words go to shared memory
+// (output row c at words 32 c .. 32 c + 31, row block rb at word rb ^ (c / 4): the 32 lanes of a store
+// hit 32 different banks), from where quads of words leave as 16-byte rows of the transposed tile.
+__device__ __forceinline__ uint32_t e4m3x4(float x0, float x1, float x2, float x3) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(x1), "f"(x0));   // x0 in the low byte
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(x3), "f"(x2));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+template <bool FROM_PLANES>
+__global__ void __launch_bounds__(kThreads) quantize_codes_kernel(
+    const void* __restrict__ src, int64_t lds, int64_t sps, int64_t rows, int64_t cols, uint8_t* __restrict__ codes,
+    int64_t ldc, int8_t* __restrict__ exps, int64_t lde, int transpose, int vec_in, int vec_out,
+    const DevState* st) {
+  if (st && (st->status != ST_RUNNING || !st->fp8_on)) return;
+  __shared__ __align__(16) uint32_t sT[128 * 32];
+  __shared__ float red[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t tr = (rows + 127) / 128, tc = (cols + 127) / 128;
+  for (int64_t b = blockIdx.x; b < tr * tc; b += gridDim.x) {
+    const int64_t bi = b / tc, bj = b % tc, r0 = bi * 128, c0 = bj * 128;
+    const int64_t gc = c0 + 4 * lane;
+    float v[4][4][4];   // [row block k][row in block][column in block]
+    float amax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t gr = r0 + 4 * (wid + 8 * k) + i;
+        float x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (gr < rows) {
+          if (FROM_PLANES) {
+            const uint16_t* pp = reinterpret_cast<const uint16_t*>(src) + gr * lds + gc;
+            if (vec_in && gc + 3 < cols) {
+              const uint2 h = *reinterpret_cast<const uint2*>(pp);
+              const uint2 m = *reinterpret_cast<const uint2*>(pp + sps);
+              const uint2 l = *reinterpret_cast<const uint2*>(pp + 2 * sps);
+              const uint32_t hw[2] = {h.x, h.y}, mw[2] = {m.x, m.y}, lw[2] = {l.x, l.y};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int sh = (j & 1) * 16;
+                x[j] = (bf16_bits_to_float((uint16_t)(hw[j >> 1] >> sh)) +
+                        bf16_bits_to_float((uint16_t)(mw[j >> 1] >> sh))) +
+                       bf16_bits_to_float((uint16_t)(lw[j >> 1] >> sh));
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (gc + j < cols)
+                  x[j] = (bf16_bits_to_float(pp[j]) + bf16_bits_to_float(pp[j + sps])) +
+                         bf16_bits_to_float(pp[j + 2 * sps]);
+            }
+          } else {
+            const float* pf = reinterpret_cast<const float*>(src) + gr * lds + gc;
+            if (vec_in && gc + 3 < cols) {
+              const float4 f = *reinterpret_cast<const float4*>(pf);
+              x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (gc + j < cols) x[j] = pf[j];
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          v[k][i][j] = x[j];
+          amax = fmaxf(amax, fabsf(x[j]));
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncthreads();   // the previous tile's readers are done with red and sT
+    if (lane == 0) red[wid] = amax;
+    __syncthreads();
+    amax = red[0];
+    for (int w = 1; w < kThreads / 32; ++w) amax = fmaxf(amax, red[w]);
+    int t = 0;
+    if (amax > 0.0f && isfinite(amax)) {
+      int e;
+      const float m = frexpf(amax, &e);
+      t = e - 9 + (m > 0.875f ? 1 : 0);
+    }
+    if (threadIdx.x == 0) exps[transpose ? bj * lde + bi : bi * lde + bj] = (int8_t)t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int rb = wid + 8 * k;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        w[i] = e4m3x4(ldexpf(v[k][i][0], -t), ldexpf(v[k][i][1], -t), ldexpf(v[k][i][2], -t),
+                      ldexpf(v[k][i][3], -t));
+      if (!transpose) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t gr = r0 + 4 * rb + i;
+          if (gr >= rows) continue;
+          uint8_t* cp = codes + gr * ldc + gc;
+          if (vec_out && gc + 3 < cols) {
+            *reinterpret_cast<uint32_t*>(cp) = w[i];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (gc + j < cols) cp[j] = (uint8_t)(w[i] >> (8 * j));
+          }
+        }
+      } else {
+        // column j of the block: bytes j of the four row words
+        const uint32_t a = __byte_perm(w[0], w[1], 0x5140), bb = __byte_perm(w[2], w[3], 0x5140);
+        const uint32_t c = __byte_perm(w[0], w[1], 0x7362), d = __byte_perm(w[2], w[3], 0x7362);
+        const uint32_t tcol[4] = {__byte_perm(a, bb, 0x5410), __byte_perm(a, bb, 0x7632), __byte_perm(c, d, 0x5410),
+                                  __byte_perm(c, d, 0x7632)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sT[(4 * lane + j) * 32 + (rb ^ lane)] = tcol[j];
+      }
+    }
+    if (transpose) {
+      __syncthreads();
+      // output row oc (source column c0 + oc), 16 source rows 16 s .. 16 s + 15 per quad of words
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = threadIdx.x + kThreads * u;
+        const int oc = idx >> 3, sq = idx & 7, g = oc >> 2;
+        if (c0 + oc >= cols) continue;
+        const uint4 x = *reinterpret_cast<const uint4*>(&sT[oc * 32 + 4 * (sq ^ (g >> 2))]);
+        // word e of the quad holds row block 4 sq + (e ^ (g & 3)): undo the swizzle's order
+        uint32_t o[4] = {x.x, x.y, x.z, x.w}, tmp;
+        if (g & 1) { tmp = o[0]; o[0] = o[1]; o[1] = tmp; tmp = o[2]; o[2] = o[3]; o[3] = tmp; }
+        if (g & 2) { tmp = o[0]; o[0] = o[2]; o[2] = tmp; tmp = o[1]; o[1] = o[3]; o[3] = tmp; }
+        const int64_t gr0 = r0 + 16 * sq;
+        uint8_t* cp = codes + (c0 + oc) * ldc + gr0;
+        if (vec_out && gr0 + 15 < rows) {
+          *reinterpret_cast<uint4*>(cp) = make_uint4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (gr0 + e < rows) cp[e] = (uint8_t)(o[e >> 2] >> (8 * (e & 3)));
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_quantize_codes(const void* src, bool from_planes, int64_t lds, int64_t sps, int64_t rows,
+                                  int64_t cols, uint8_t* codes, int64_t ldc, int8_t* exps, int64_t lde, bool transpose,
+                                  const DevState* st, cudaStream_t s) {
+  const int64_t tiles = ((rows + 127) / 128) * ((cols + 127) / 128);
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = (int)(tiles < 8192 ? tiles : 8192);
+  const uintptr_t sa = reinterpret_cast<uintptr_t>(src), ca = reinterpret_cast<uintptr_t>(codes);
+  // vector accesses: 16-byte float4 (8-byte uint2 for the planes) rows and 4-byte (transposed: 16-byte)
+  // code words, where the base and the pitches keep every one aligned
+  const int vec_in = from_planes ? (sa % 8 == 0 && lds % 4 == 0 && sps % 4 == 0) : (sa % 16 == 0 && lds % 4 == 0);
+  const int vec_out = transpose ? (ca % 16 == 0 && ldc % 16 == 0) : (ca % 4 == 0 && ldc % 4 == 0);
+  if (from_planes)
+    quantize_codes_kernel<true><<<grid, kThreads, 0, s>>>(src, lds, sps, rows, cols, codes, ldc, exps, lde,
+                                                         transpose ? 1 : 0, vec_in, vec_out, st);
+  else
+    quantize_codes_kernel<false><<<grid, kThreads, 0, s>>>(src, lds, sps, rows, cols, codes, ldc, exps, lde,
+                                                          transpose ? 1 : 0, vec_in, vec_out, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_quantize_e4m3_planes(const uint16_t* src, int64_t ldp, int64_t sps, int64_t rows, int64_t cols,
                                         uint16_t* dst, int64_t ldd, const DevState* st, cudaStream_t s) {
   const int64_t tiles = ((rows + 127) / 128) * ((cols + 127) / 128);

@@ -117,8 +117,13 @@ struct polar_plan_s {
   uint16_t* Xp[2] = {nullptr, nullptr};  // BF16 planes of X (double buffer)
   uint16_t* Gp = nullptr;                // BF16 planes of G
   uint16_t* Ap = nullptr;                // BF16 planes of A (for H)
-  uint16_t* Xq = nullptr;                // FP8 schedule: E4M3-quantized X_k and G (one BF16 plane each)
-  uint16_t* Gq = nullptr;
+  uint8_t* Xq = nullptr;                 // FP8 schedule: E4M3 codes of X_k (m x n, for the update), of X_k^T
+  uint8_t* XqT = nullptr;                // (n x m, for the Gram) and of G (n x n), rows padded to 16 bytes,
+  uint8_t* Gq = nullptr;                 // and the exponents of their 128 x 128 tiles
+  int8_t* eX = nullptr;
+  int8_t* eXT = nullptr;
+  int8_t* eG = nullptr;
+  int64_t kpm = 0, kpn = 0;              // code row pitches: m and n rounded up to 16
   int64_t ldp = 0;                       // plane row pitch (elements)
   int64_t xps = 0, gps = 0;              // plane strides (elements)
   double* partials = nullptr;
@@ -272,12 +277,21 @@ polar_status_t plan_setup(polar_plan_s* p) {
     CK(cudaMemset(v, 0, (size_t)p->P * p->xps * 2));
     p->Ap = (uint16_t*)v;
     if (p->prec == POLAR_SCHED_FP8_BF16_X3) {
-      if ((r = plan_alloc(p, (size_t)p->xps * 2, &v)) != POLAR_OK) return r;
-      CK(cudaMemset(v, 0, (size_t)p->xps * 2));
-      p->Xq = (uint16_t*)v;
-      if ((r = plan_alloc(p, (size_t)p->gps * 2, &v)) != POLAR_OK) return r;
-      CK(cudaMemset(v, 0, (size_t)p->gps * 2));
-      p->Gq = (uint16_t*)v;
+      p->kpm = round_up(m, 16);
+      p->kpn = round_up(n, 16);
+      const int64_t mb = (m + 127) / 128, nb = (n + 127) / 128;
+      const size_t bx = (size_t)round_up(m * p->kpn, 256), bxt = (size_t)round_up(n * p->kpm, 256),
+                   bg = (size_t)round_up(n * p->kpn, 256), be = (size_t)round_up(mb * nb, 256) * 2 +
+                                                                (size_t)round_up(nb * nb, 256);
+      if ((r = plan_alloc(p, bx + bxt + bg + be, &v)) != POLAR_OK) return r;
+      CK(cudaMemset(v, 0, bx + bxt + bg + be));
+      uint8_t* w = (uint8_t*)v;
+      p->Xq = w;
+      p->XqT = w + bx;
+      p->Gq = w + bx + bxt;
+      p->eX = (int8_t*)(w + bx + bxt + bg);
+      p->eXT = p->eX + round_up(mb * nb, 256);
+      p->eG = p->eXT + round_up(mb * nb, 256);
     }
   }
   if ((r = plan_alloc(p, (size_t)n * p->ldg * 4, &v)) != POLAR_OK) return r;
@@ -389,21 +403,29 @@ TcOperand op_planes(const uint16_t* planes, int64_t rows, int64_t cols, int64_t 
 cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
   const uint16_t* Xk = p->Xp[k & 1];
   if (rule.sched == 2) {
-    // FP8 phase: X_k quantized per 128 x 128 tile, its Gram from that one plane (both launches are
-    // enqueued; the one for the phase that is not current returns at once)
-    cudaError_t e = launch_quantize_e4m3_planes(Xk, p->ldp, p->xps, p->m, p->n, p->Xq, p->ldp, p->st, s);
+    // FP8 phase: the E4M3 codes of X_k (per 128 x 128 tile, with the tiles' exponents) as the Gram's
+    // K-major operands X_k^T, and as the update's X_k; the Gram on the FP8 tensor cores (both launches
+    // are enqueued; the one for the phase that is not current returns at once)
+    const int64_t mb = (p->m + 127) / 128, nb = (p->n + 127) / 128;
+    cudaError_t e = launch_quantize_codes(Xk, true, p->ldp, p->xps, p->m, p->n, p->XqT, p->kpm, p->eXT, mb, true,
+                                          p->st, s);
     if (e != cudaSuccess) return e;
+    if ((e = launch_quantize_codes(Xk, true, p->ldp, p->xps, p->m, p->n, p->Xq, p->kpn, p->eX, nb, false, p->st, s)) !=
+        cudaSuccess)
+      return e;
     TcArgs q{};
     q.M = p->n; q.N = p->n; q.K = p->m;
-    q.a = op_planes(p->Xq, p->m, p->n, p->ldp, p->xps, 0);
+    q.a = op_planes((const uint16_t*)p->XqT, p->n, p->m, p->kpm, 0, 1);
     q.b = q.a;
     q.nplanes = 1;
     q.epi = TC_EPI_GRAM; q.triangular = 1;
     q.out_planes = p->Gp; q.ldo = p->ldp; q.out_plane_stride = p->gps; q.out_nplanes = kStoredPlanes;
     q.partials = p->partials; q.st = p->st;
     q.planes_dyn = &p->st->fp8_on;
-    if ((e = launch_tc_gemm(q, s)) != cudaSuccess) return e;
-    p->launches += 2;
+    q.a_exp = p->eXT; q.lde_a = mb;
+    q.b_exp = p->eXT; q.lde_b = mb;
+    if ((e = launch_tc_gemm_fp8(q, s)) != cudaSuccess) return e;
+    p->launches += 3;
   }
   TcArgs g{};
   g.M = p->n; g.N = p->n; g.K = p->m;
@@ -431,20 +453,25 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
 
 cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cudaStream_t s) {
   if (rule.sched == 2) {
-    // FP8 phase: X_k (quantized with the Gram) times the quantized G
-    cudaError_t e = launch_quantize_e4m3_planes(p->Gp, p->ldp, p->gps, p->n, p->n, p->Gq, p->ldp, p->st, s);
+    // FP8 phase: X_k's codes (made with the Gram) times the codes of G (symmetric: its rows are the
+    // K-major B operand), on the FP8 tensor cores
+    const int64_t nb = (p->n + 127) / 128;
+    cudaError_t e = launch_quantize_codes(p->Gp, true, p->ldp, p->gps, p->n, p->n, p->Gq, p->kpn, p->eG, nb, false,
+                                          p->st, s);
     if (e != cudaSuccess) return e;
     TcArgs q{};
     q.M = p->m; q.N = p->n; q.K = p->n;
-    q.a = op_planes(p->Xq, p->m, p->n, p->ldp, p->xps, 1);
-    q.b = op_planes(p->Gq, p->n, p->n, p->ldp, p->gps, 0);
+    q.a = op_planes((const uint16_t*)p->Xq, p->m, p->n, p->kpn, 0, 1);
+    q.b = op_planes((const uint16_t*)p->Gq, p->n, p->n, p->kpn, 0, 1);
+    q.a_exp = p->eX; q.lde_a = nb;
+    q.b_exp = p->eG; q.lde_b = nb;
     q.nplanes = 1;
     q.epi = TC_EPI_NS;
     q.x_planes = p->Xp[k & 1]; q.ldxp = p->ldp; q.x_plane_stride = p->xps;
     q.out_planes = p->Xp[(k + 1) & 1]; q.ldo = p->ldp; q.out_plane_stride = p->xps; q.out_nplanes = kStoredPlanes;
     q.st = p->st;
     q.planes_dyn = &p->st->fp8_on;
-    if ((e = launch_tc_gemm(q, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_gemm_fp8(q, s)) != cudaSuccess) return e;
     p->launches += 2;
   }
   TcArgs u{};
@@ -801,6 +828,54 @@ polar_status_t polar_gemm(int transA, int transB, int64_t M, int64_t N, int64_t 
   g.epi = TC_EPI_STORE;
   g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
   return launch_tc_gemm(g, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+polar_status_t polar_gemm_fp8(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                              polar_stream_t stream) {
+  if (M < 0 || N < 0 || K < 0) return POLAR_EINVAL;
+  if (M == 0 || N == 0) return POLAR_OK;
+  if (!C || ldc < N) return POLAR_EINVAL;
+  if (K > 0 && (!A || !B)) return POLAR_EINVAL;
+  const int64_t a_rows = transA ? K : M, a_cols = transA ? M : K;
+  const int64_t b_rows = transB ? N : K, b_cols = transB ? K : N;
+  if (K > 0 && (lda < a_cols || ldb < b_cols)) return POLAR_EINVAL;
+  if (!device_ok()) { cudaGetLastError(); return POLAR_ECUDA; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0) {
+    SimtArgs g{};
+    g.M = M; g.N = N; g.K = 0; g.A = C; g.lda = ldc; g.a_kmajor = 1; g.B = C; g.ldb = ldc; g.b_kmajor = 1;
+    g.C = C; g.ldc = ldc; g.alpha = 0.f; g.beta = beta;
+    return launch_simt_gemm(g, SIMT_EPI_STORE, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+  }
+  if (!tc_available()) return POLAR_ENOTSUP;
+  // K-major codes of op(A) (M x K) and op(B)^T (N x K), rows padded to 16 bytes, and the tiles' exponents
+  const int64_t kp = round_up(K, 16), kb = (K + 127) / 128;
+  const int64_t mb = (M + 127) / 128, nb = (N + 127) / 128;
+  const size_t oa = 0, ob = round_up(M * kp, 256), oea = ob + round_up(N * kp, 256), oeb = oea + round_up(mb * kb, 256);
+  const size_t bytes = oeb + round_up(nb * kb, 256);
+  void* scr = nullptr;
+  polar_status_t r = scratch_get(bytes, &scr);
+  if (r != POLAR_OK) return r;
+  uint8_t* w = (uint8_t*)scr;
+  uint8_t* ca = w + oa;
+  uint8_t* cb = w + ob;
+  int8_t* ea = (int8_t*)(w + oea);
+  int8_t* eb = (int8_t*)(w + oeb);
+  // op(A) = A (stored M x K) or A^T (stored K x M: transposed into M x K); op(B)^T = B^T (B stored K x N:
+  // transposed into N x K) or B (stored N x K)
+  CK(launch_quantize_codes(A, false, lda, 0, a_rows, a_cols, ca, kp, ea, kb, transA != 0, nullptr, s));
+  CK(launch_quantize_codes(B, false, ldb, 0, b_rows, b_cols, cb, kp, eb, kb, transB == 0, nullptr, s));
+  TcArgs g{};
+  g.M = M; g.N = N; g.K = K;
+  g.a = op_planes((const uint16_t*)ca, M, K, kp, 0, 1);
+  g.b = op_planes((const uint16_t*)cb, N, K, kp, 0, 1);
+  g.nplanes = 1;
+  g.epi = TC_EPI_STORE;
+  g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
+  g.a_exp = ea; g.lde_a = kb;
+  g.b_exp = eb; g.lde_b = kb;
+  return launch_tc_gemm_fp8(g, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 polar_status_t polar_syrk(int64_t n, int64_t k, float alpha, const float* A, int64_t lda, float beta, float* C,

@@ -95,6 +95,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
+// One FP8 MMA (.kind::f8f6f4; the operand formats are in the instruction descriptor).
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -120,6 +131,22 @@ __device__ __forceinline__ void add16_packed(float* acc, const float (&v)[16]) {
         "mov.b64 {%0, %1}, c;\n\t}"
         : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
         : "f"(v[2 * i]), "f"(v[2 * i + 1]));
+  }
+}
+
+// acc += v * sc, two lanes per instruction, one rounding: with sc a power of two the product is
+// exact, so this equals the round-to-nearest add of the scaled values.
+__device__ __forceinline__ void fma16_packed(float* acc, const float (&v)[16], float sc) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    asm("{\n\t.reg .b64 a, b, c;\n\t"
+        "mov.b64 a, {%0, %1};\n\t"
+        "mov.b64 b, {%2, %3};\n\t"
+        "mov.b64 c, {%4, %4};\n\t"
+        "fma.rn.f32x2 a, b, c, a;\n\t"
+        "mov.b64 {%0, %1}, a;\n\t}"
+        : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+        : "f"(v[2 * i]), "f"(v[2 * i + 1]), "f"(sc));
   }
 }
 

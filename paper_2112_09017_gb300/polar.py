@@ -88,6 +88,7 @@ def load():
         "polar_plan_destroy": (None, [vp]),
         "polar_gemm": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
         "polar_gemm_noalloc": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
+        "polar_gemm_fp8": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
         "polar_syrk": (i32, [i64, i64, f32, vp, i64, f32, vp, i64, i32, vp]),
         "polar_split_bf16": (i32, [vp, i64, i32, vp, vp]),
         "polar_ns_inverse": (i32, [vp, i64, i64, i64, vp, i64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
@@ -278,6 +279,20 @@ def polar_gemm(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, prec
                           B.stride(0), float(beta), _ptr(C_), C_.stride(0), int(prec), _stream(stream))
     if r != POLAR_OK:
         raise PolarError(r, "polar_gemm")
+
+
+def polar_gemm_fp8(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, stream=None):
+    """C_ = alpha Q(op(A)) Q(op(B)) + beta C_ on the FP8 tensor cores (per-128 x 128-tile E4M3 operands)."""
+    _check_f32_2d(A, "A"); _check_f32_2d(B, "B"); _check_f32_2d(C_, "C")
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    N = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != K or tuple(C_.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    r = load().polar_gemm_fp8(int(trans_a), int(trans_b), M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                              B.stride(0), float(beta), _ptr(C_), C_.stride(0), _stream(stream))
+    if r != POLAR_OK:
+        raise PolarError(r, "polar_gemm_fp8")
 
 
 def polar_gemm_noalloc(A, B, C_, trans_a=False, trans_b=False, alpha=1.0, beta=0.0, prec=POLAR_FP32, stream=None,

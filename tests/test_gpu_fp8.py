@@ -10,7 +10,7 @@ import pytest
 from oracle.precision import quantize_tiles_e4m3
 from paper_2112_09017_gb300 import synth
 
-from .gpu_util import metrics, to_np
+from .gpu_util import U32, metrics, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -89,3 +89,86 @@ def test_fp8_schedule_not_for_batched(lib):
     with pytest.raises(lib.PolarError) as e:
         lib.polar_batched_plan_create([64, 128], [64, 64], o)
     assert e.value.code == lib.POLAR_ENOTSUP
+
+
+FP8_SHAPES = [(1, 1, 1), (130, 260, 200), (257, 129, 300), (64, 520, 1000), (300, 300, 129)]
+
+
+def _ops(rng, m, n, k, ta, tb, draw):
+    a = draw(rng, (k, m) if ta else (m, k))
+    b = draw(rng, (n, k) if tb else (k, n))
+    return a, b, (a.T if ta else a), (b.T if tb else b)
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+@pytest.mark.parametrize("mnk", FP8_SHAPES)
+def test_gemm_fp8_small_integers_exact(lib, ta, tb, mnk):
+    """Integers in [-8, 8] are E4M3 codes times the tile's power of two, and their products and
+    sums stay below 2^24: the FP8 product equals the integer product bit for bit."""
+    import torch
+    m, n, k = mnk
+    rng = np.random.default_rng(m * 7 + n * 3 + k + 2 * ta + tb)
+    a, b, oa, ob = _ops(rng, m, n, k, ta, tb,
+                        lambda r, s: r.integers(-8, 9, s).astype(np.float32))
+    assert np.array_equal(quantize_tiles_e4m3(np.ascontiguousarray(oa)), oa)
+    C = torch.full((m, n), np.nan, dtype=torch.float32, device="cuda")
+    lib.polar_gemm_fp8(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), C, ta, tb)
+    want = oa.astype(np.float64) @ ob.astype(np.float64)
+    assert np.array_equal(to_np(C).astype(np.float64), want)
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("mnk", FP8_SHAPES[1:])
+def test_gemm_fp8_matches_quantized_product(lib, ta, tb, mnk):
+    """Rows of very different scales: the product is the exact product of the oracle's per-tile
+    E4M3 roundings of op(A) and op(B), within float32 accumulation of k terms (2^-20 per term
+    leaves room for the tensor cores' truncating accumulation), and beta C adds two roundings."""
+    import torch
+    m, n, k = mnk
+    rng = np.random.default_rng(m + 5 * n + 11 * k + ta + 2 * tb)
+    a, b, oa, ob = _ops(rng, m, n, k, ta, tb,
+                        lambda r, s: (r.standard_normal(s) * np.exp(r.uniform(-6, 6, (s[0], 1)))).astype(np.float32))
+    c0 = rng.standard_normal((m, n)).astype(np.float32)
+    alpha, beta = 0.75, -1.25
+    C = torch.from_numpy(c0).cuda()
+    lib.polar_gemm_fp8(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), C, ta, tb, alpha, beta)
+    qa = quantize_tiles_e4m3(np.ascontiguousarray(oa)).astype(np.float64)
+    qb = quantize_tiles_e4m3(np.ascontiguousarray(ob)).astype(np.float64)
+    want = alpha * (qa @ qb) + beta * c0.astype(np.float64)
+    bound = abs(alpha) * (k + 4) * 2.0 ** -20 * (np.abs(qa) @ np.abs(qb)) + 2 * U32 * abs(beta) * np.abs(c0) + 1e-30
+    err = np.abs(to_np(C).astype(np.float64) - want)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # and not the unquantized product: the E4M3 rounding is visible at this size
+    exact = alpha * (oa.astype(np.float64) @ ob.astype(np.float64)) + beta * c0.astype(np.float64)
+    assert np.max(np.abs(exact - want)) > 100 * np.max(err)
+
+
+def test_gemm_fp8_zero_k_scales_c(lib):
+    import torch
+    C = torch.ones((3, 5), dtype=torch.float32, device="cuda")
+    A = torch.zeros((3, 0), dtype=torch.float32, device="cuda")
+    B = torch.zeros((0, 5), dtype=torch.float32, device="cuda")
+    lib.polar_gemm_fp8(A, B, C, beta=2.0)
+    assert np.array_equal(to_np(C), np.full((3, 5), 2.0, dtype=np.float32))
+
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("shape", [(1, 1), (130, 260), (257, 129), (300, 520)])
+def test_gemm_fp8_identity_gives_the_oracles_codes(lib, trans, shape):
+    """Q(I) = I, so Q(op(A)) I and I Q(op(B)) are the oracle's per-tile E4M3 roundings bit for bit:
+    both operands' codes, exponents and transposed layouts, tile by tile."""
+    import torch
+    rng = np.random.default_rng(shape[0] * 13 + shape[1] + trans)
+    r, c = shape
+    x = (rng.standard_normal((r, c)) * np.exp(rng.uniform(-9, 9, (r, 1)))).astype(np.float32)
+    opx = x.T if trans else x
+    want = quantize_tiles_e4m3(np.ascontiguousarray(opx))
+    X = torch.from_numpy(x).cuda()
+    m, k = opx.shape
+    C = torch.full((m, k), np.nan, dtype=torch.float32, device="cuda")
+    lib.polar_gemm_fp8(X, torch.eye(k, device="cuda"), C, trans, False)
+    assert np.array_equal(to_np(C), want)
+    C = torch.full((m, k), np.nan, dtype=torch.float32, device="cuda")
+    lib.polar_gemm_fp8(torch.eye(m, device="cuda"), X, C, False, trans)
+    assert np.array_equal(to_np(C), want)
