@@ -122,3 +122,38 @@ def test_batched_preconditioned_matches_oracle(lib, torch_cuda):
         assert abs(iters[i] - ref["iters_at"]) <= 1, (i, iters[i], ref["iters_at"])
         met = metrics(a, to_np(Us[i]), to_np(Hs[i]), ref["U"])
         assert met["orth"] <= 5e-6 and met["bwd"] <= 5e-6, (i, met)
+
+
+def test_bound_buffers_match_the_list_call(lib, torch_cuda):
+    """polar_batched_bind checks the tensors once; runs with the bound buffers give the list call's
+    factors bit for bit, the buffers refuse another plan, and an unbound run still needs U and H."""
+    torch = torch_cuda
+    sizes = [(64, 64), (130, 65), (96, 33), (400, 200)]
+    mats = [synth.matrix_with_spectrum(m, n, synth.logspace_spectrum(n, 1e-2), 300 + i)
+            for i, (m, n) in enumerate(sizes)]
+    ms = [a.shape[0] for a in mats]
+    ns = [a.shape[1] for a in mats]
+    o = lib.polar_default_options()
+    o.prec = lib.POLAR_BF16X6
+    plan = lib.polar_batched_plan_create(ms, ns, o)
+    other = lib.polar_batched_plan_create(ms, ns, o)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    U1 = [torch.zeros((m, n), device="cuda") for m, n in zip(ms, ns)]
+    H1 = [torch.zeros((n, n), device="cuda") for n in ns]
+    U2 = [torch.zeros((m, n), device="cuda") for m, n in zip(ms, ns)]
+    H2 = [torch.zeros((n, n), device="cuda") for n in ns]
+    lib.polar_batched_run(plan, As, U1, H1)
+    bound = lib.polar_batched_bind(plan, As, U2, H2)
+    for _ in range(2):
+        lib.polar_batched_run(plan, bound)
+    torch.cuda.synchronize()
+    for a, b in zip(U1 + H1, U2 + H2):
+        assert torch.equal(a, b)
+    with pytest.raises(ValueError):
+        lib.polar_batched_run(other, bound)
+    with pytest.raises(ValueError):
+        lib.polar_batched_run(plan, As)
+    with pytest.raises(ValueError):
+        lib.polar_batched_bind(plan, As[:-1], U2[:-1], H2[:-1])
+    lib.polar_plan_destroy(other)
+    lib.polar_plan_destroy(plan)
