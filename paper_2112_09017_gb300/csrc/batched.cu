@@ -73,8 +73,17 @@ __global__ void b_norm_kernel(const float* const* __restrict__ A, const BMeta* _
   const BMeta& mt = meta[p];
   const float* a = A[p];
   double acc = 0.0;
-  const int64_t total = mt.m * mt.n;
-  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+  const int64_t total = mt.m * mt.n, step = blockDim.x;
+  int64_t i = threadIdx.x;
+  // eight loads in flight per thread; each thread still adds its elements in increasing order
+  for (; i + 7 * step < total; i += 8 * step) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = a[i + j * step];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc = fma((double)v[j], (double)v[j], acc);
+  }
+  for (; i < total; i += step) {
     const double v = (double)a[i];
     acc = fma(v, v, acc);
   }
@@ -100,6 +109,11 @@ __global__ void b_norm_kernel(const float* const* __restrict__ A, const BMeta* _
   }
 }
 
+// A block's threads as rows of `tw` lanes (the smallest of 32, 64, 128, 256 that covers n, at
+// most 256), so that narrow problems keep every thread busy: thread t takes column t % tw of
+// row t / tw of each group of blockDim / tw rows.
+__device__ __forceinline__ int row_lanes(int64_t n) { return n > 128 ? 256 : n > 64 ? 128 : n > 32 ? 64 : 32; }
+
 // X_0 = A_p / ||A_p||_F as three planes, and P planes of A_p (for H). Grid (count, Y).
 __global__ void b_scale_split_kernel(const float* const* __restrict__ A, const BMeta* __restrict__ meta,
                                      const DevState* __restrict__ st, int P) {
@@ -108,8 +122,9 @@ __global__ void b_scale_split_kernel(const float* const* __restrict__ A, const B
   const BMeta& mt = meta[p];
   const float* a = A[p];
   const float s = (float)st[p].normA;
-  for (int64_t r = blockIdx.y; r < mt.m; r += gridDim.y) {
-    for (int64_t c = threadIdx.x; c < mt.n; c += blockDim.x) {
+  const int tw = row_lanes(mt.n), rpb = (int)blockDim.x / tw;
+  for (int64_t r = (int64_t)blockIdx.y * rpb + threadIdx.x / tw; r < mt.m; r += (int64_t)gridDim.y * rpb) {
+    for (int64_t c = threadIdx.x % tw; c < mt.n; c += tw) {
       const float av = a[r * mt.n + c];
       const int64_t o = r * mt.ldp + c;
       uint16_t q[3];
@@ -186,8 +201,9 @@ __global__ void b_u_kernel(const BMeta* __restrict__ meta, const DevState* __res
   const BMeta& mt = meta[p];
   const uint16_t* X = mt.xp[st[p].iters & 1];
   float* u = U[p];
-  for (int64_t r = blockIdx.y; r < mt.m; r += gridDim.y)
-    for (int64_t c = threadIdx.x; c < mt.n; c += blockDim.x) {
+  const int tw = row_lanes(mt.n), rpb = (int)blockDim.x / tw;
+  for (int64_t r = (int64_t)blockIdx.y * rpb + threadIdx.x / tw; r < mt.m; r += (int64_t)gridDim.y * rpb)
+    for (int64_t c = threadIdx.x % tw; c < mt.n; c += tw) {
       const int64_t o = r * mt.ldp + c;
       u[r * mt.n + c] = (bf16_to_f32_dev(X[o]) + bf16_to_f32_dev(X[mt.xps + o])) + bf16_to_f32_dev(X[2 * mt.xps + o]);
     }
