@@ -207,6 +207,8 @@ cudaError_t launch_tc_gemm(const TcArgs& a_in, cudaStream_t s) {
 cudaError_t launch_tc_gemm_fp8(const TcArgs& a_in, cudaStream_t s) {
   TcArgs a = a_in;
   a.slice_stages = 1;                 // one 128-K block per slice: its scale is applied at the promotion
+  if (a.a_uni && a.b_uni && a.fp8_run <= 0) a.fp8_run = 8;   // tiles under one scale: 1024 K per slice
+  if (!a.a_uni || !a.b_uni) a.a_uni = a.b_uni = nullptr;
   a.withhold_tma = withhold_tma();
   if (!a.st && !a.err_out) a.err_out = default_error_word();
   if (a.M <= 0 || a.N <= 0 || a.K <= 0 || !a.a_exp || !a.b_exp || a.lde_a < (a.K + 127) / 128 ||

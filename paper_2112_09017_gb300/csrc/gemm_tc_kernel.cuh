@@ -332,6 +332,16 @@ struct SingleSrc {
     c.nk = nk;
     c.args = args;
     c.sl = args->slice_stages > 0 ? args->slice_stages : 1;
+    if (args->a_uni) {
+      // FP8: a tile whose A block and B blocks each keep one exponent along K has one scale per
+      // epilogue half, so its K blocks accumulate fp8_run at a time before the promotion
+      const int64_t nb = (args->N + 127) / 128, j0 = c.bj * (BN / 128);
+      bool u = args->a_uni[c.bi] != 0;
+#pragma unroll
+      for (int h = 0; h < BN / 128; ++h)
+        if (j0 + h < nb) u = u && args->b_uni[j0 + h] != 0;
+      if (u) c.sl = args->fp8_run;
+    }
     return true;
   }
 };
@@ -550,11 +560,12 @@ __device__ __noinline__ void role_epilogue(const Src& src, uint32_t tmem_base, B
       if (!mbar_wait(br.tfull0 + 8 * bslot, buf_phase, abort_flag)) { ok = false; break; }
       tc_fence_after();
       if (p.a_exp) {
-        // FP8 operands: the slice is one 128-K block, scaled by its tiles' powers of two (exact). Lane
+        // FP8 operands: the slice is one 128-K block, scaled by its tiles' powers of two (exact), or,
+        // in a tile whose blocks keep one exponent along K, several blocks under that one scale. Lane
         // l holds the exponent sum of slice 32 j + l, fetched once per 32 slices; a half tile past N
         // has no exponent (its columns are not stored).
         if ((sl & 31) == 0) {
-          const int64_t bcol = ctx.bj * (TN / 128) + half, s2 = sl + lane;
+          const int64_t bcol = ctx.bj * (TN / 128) + half, s2 = ctx.sl > 1 ? 0 : sl + lane;
           e_sum = (s2 < nslices && bcol * 128 < p.N)
                       ? (int)p.a_exp[ctx.bi * p.lde_a + s2] + (int)p.b_exp[bcol * p.lde_b + s2]
                       : 0;

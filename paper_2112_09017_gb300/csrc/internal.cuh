@@ -122,10 +122,12 @@ cudaError_t launch_quantize_e4m3_planes(const uint16_t* src, int64_t ldp, int64_
                                         uint16_t* dst, int64_t ldd, const DevState* st, cudaStream_t s);
 // FP8 operands for the E4M3 tensor-core products: the E4M3 codes of every 128 x 128 tile of src (float32, or
 // three BF16 planes with from_planes) divided by that tile's power of two, and the exponents, optionally
-// transposed (codes and exponent table both); skipped unless st is null or RUNNING in its FP8 phase.
+// transposed (codes and exponent table both); with uni, also one byte per 128-row block of the codes (per
+// column block of src when transposed): 1 when every exponent of that block is the same. Skipped unless
+// st is null or RUNNING in its FP8 phase.
 cudaError_t launch_quantize_codes(const void* src, bool from_planes, int64_t lds, int64_t sps, int64_t rows,
                                   int64_t cols, uint8_t* codes, int64_t ldc, int8_t* exps, int64_t lde, bool transpose,
-                                  const DevState* st, cudaStream_t s);
+                                  uint8_t* uni, const DevState* st, cudaStream_t s);
 // The same from a float32 matrix into a float32 matrix (library service).
 cudaError_t launch_quantize_e4m3_f32(const float* src, int64_t lds, int64_t rows, int64_t cols, float* dst,
                                      int64_t ldd, cudaStream_t s);
@@ -188,6 +190,9 @@ struct TcArgs {
   const int8_t* a_exp;                            // FP8 operands: power-of-two exponents of A's 128 x 128 tiles,
   const int8_t* b_exp;                            // a_exp[M block * lde_a + K block], b_exp[N block * lde_b +
   int64_t lde_a, lde_b;                           // K block]; each 128-K slice is promoted times 2^(ea + eb)
+  const uint8_t* a_uni;                           // FP8: per 128-row block of A (of B), 1 when all its K blocks
+  const uint8_t* b_uni;                           // share one exponent; a tile whose blocks all do accumulates
+  int fp8_run;                                    // fp8_run K blocks per slice under its one scale
   unsigned int* err_out;                          // without st: word set to 1 when a bounded wait expired
                                                   // (null: the device-wide word read by tc_take_error)
 };

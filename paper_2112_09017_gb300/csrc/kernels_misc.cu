@@ -696,9 +696,22 @@ __global__ void __launch_bounds__(kThreads) quantize_codes_kernel(
   }
 }
 
+// uni[r] = 1 when exps[r * lde + k] is the same for every k < nk (block rows r < nr).
+__global__ void uniform_exps_kernel(const int8_t* __restrict__ exps, int64_t lde, int64_t nr, int64_t nk,
+                                    uint8_t* __restrict__ uni, const DevState* st) {
+  if (st && (st->status != ST_RUNNING || !st->fp8_on)) return;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int8_t* e = exps + r * lde;
+  const int8_t e0 = e[0];
+  uint8_t u = 1;
+  for (int64_t k = 1; k < nk; ++k) u &= (uint8_t)(e[k] == e0);
+  uni[r] = u;
+}
+
 cudaError_t launch_quantize_codes(const void* src, bool from_planes, int64_t lds, int64_t sps, int64_t rows,
                                   int64_t cols, uint8_t* codes, int64_t ldc, int8_t* exps, int64_t lde, bool transpose,
-                                  const DevState* st, cudaStream_t s) {
+                                  uint8_t* uni, const DevState* st, cudaStream_t s) {
   const int64_t tiles = ((rows + 127) / 128) * ((cols + 127) / 128);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < 8192 ? tiles : 8192);
@@ -713,6 +726,11 @@ cudaError_t launch_quantize_codes(const void* src, bool from_planes, int64_t lds
   else
     quantize_codes_kernel<false><<<grid, kThreads, 0, s>>>(src, lds, sps, rows, cols, codes, ldc, exps, lde,
                                                           transpose ? 1 : 0, vec_in, vec_out, st);
+  if (uni) {
+    const int64_t tr = (rows + 127) / 128, tc = (cols + 127) / 128;
+    const int64_t nr = transpose ? tc : tr, nk = transpose ? tr : tc;
+    uniform_exps_kernel<<<(int)((nr + kThreads - 1) / kThreads), kThreads, 0, s>>>(exps, lde, nr, nk, uni, st);
+  }
   return cudaGetLastError();
 }
 

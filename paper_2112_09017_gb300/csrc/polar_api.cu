@@ -123,6 +123,9 @@ struct polar_plan_s {
   int8_t* eX = nullptr;
   int8_t* eXT = nullptr;
   int8_t* eG = nullptr;
+  uint8_t* uX = nullptr;                 // per 128-row block of those codes: one exponent along K
+  uint8_t* uXT = nullptr;
+  uint8_t* uG = nullptr;
   int64_t kpm = 0, kpn = 0;              // code row pitches: m and n rounded up to 16
   int64_t ldp = 0;                       // plane row pitch (elements)
   int64_t xps = 0, gps = 0;              // plane strides (elements)
@@ -282,7 +285,8 @@ polar_status_t plan_setup(polar_plan_s* p) {
       const int64_t mb = (m + 127) / 128, nb = (n + 127) / 128;
       const size_t bx = (size_t)round_up(m * p->kpn, 256), bxt = (size_t)round_up(n * p->kpm, 256),
                    bg = (size_t)round_up(n * p->kpn, 256), be = (size_t)round_up(mb * nb, 256) * 2 +
-                                                                (size_t)round_up(nb * nb, 256);
+                                                                (size_t)round_up(nb * nb, 256) +
+                                                                (size_t)round_up(mb, 256) + 2 * (size_t)round_up(nb, 256);
       if ((r = plan_alloc(p, bx + bxt + bg + be, &v)) != POLAR_OK) return r;
       CK(cudaMemset(v, 0, bx + bxt + bg + be));
       uint8_t* w = (uint8_t*)v;
@@ -292,6 +296,9 @@ polar_status_t plan_setup(polar_plan_s* p) {
       p->eX = (int8_t*)(w + bx + bxt + bg);
       p->eXT = p->eX + round_up(mb * nb, 256);
       p->eG = p->eXT + round_up(mb * nb, 256);
+      p->uX = reinterpret_cast<uint8_t*>(p->eG + round_up(nb * nb, 256));
+      p->uXT = p->uX + round_up(mb, 256);
+      p->uG = p->uXT + round_up(nb, 256);
     }
   }
   if ((r = plan_alloc(p, (size_t)n * p->ldg * 4, &v)) != POLAR_OK) return r;
@@ -408,10 +415,10 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
     // are enqueued; the one for the phase that is not current returns at once)
     const int64_t mb = (p->m + 127) / 128, nb = (p->n + 127) / 128;
     cudaError_t e = launch_quantize_codes(Xk, true, p->ldp, p->xps, p->m, p->n, p->XqT, p->kpm, p->eXT, mb, true,
-                                          p->st, s);
+                                          p->uXT, p->st, s);
     if (e != cudaSuccess) return e;
-    if ((e = launch_quantize_codes(Xk, true, p->ldp, p->xps, p->m, p->n, p->Xq, p->kpn, p->eX, nb, false, p->st, s)) !=
-        cudaSuccess)
+    if ((e = launch_quantize_codes(Xk, true, p->ldp, p->xps, p->m, p->n, p->Xq, p->kpn, p->eX, nb, false, p->uX,
+                                   p->st, s)) != cudaSuccess)
       return e;
     TcArgs q{};
     q.M = p->n; q.N = p->n; q.K = p->m;
@@ -424,8 +431,9 @@ cudaError_t enqueue_gram_tc(polar_plan_s* p, int k, const StopRule& rule, cudaSt
     q.planes_dyn = &p->st->fp8_on;
     q.a_exp = p->eXT; q.lde_a = mb;
     q.b_exp = p->eXT; q.lde_b = mb;
+    q.a_uni = p->uXT; q.b_uni = p->uXT;
     if ((e = launch_tc_gemm_fp8(q, s)) != cudaSuccess) return e;
-    p->launches += 3;
+    p->launches += 5;
   }
   TcArgs g{};
   g.M = p->n; g.N = p->n; g.K = p->m;
@@ -457,7 +465,7 @@ cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cuda
     // K-major B operand), on the FP8 tensor cores
     const int64_t nb = (p->n + 127) / 128;
     cudaError_t e = launch_quantize_codes(p->Gp, true, p->ldp, p->gps, p->n, p->n, p->Gq, p->kpn, p->eG, nb, false,
-                                          p->st, s);
+                                          p->uG, p->st, s);
     if (e != cudaSuccess) return e;
     TcArgs q{};
     q.M = p->m; q.N = p->n; q.K = p->n;
@@ -465,6 +473,7 @@ cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cuda
     q.b = op_planes((const uint16_t*)p->Gq, p->n, p->n, p->kpn, 0, 1);
     q.a_exp = p->eX; q.lde_a = nb;
     q.b_exp = p->eG; q.lde_b = nb;
+    q.a_uni = p->uX; q.b_uni = p->uG;
     q.nplanes = 1;
     q.epi = TC_EPI_NS;
     q.x_planes = p->Xp[k & 1]; q.ldxp = p->ldp; q.x_plane_stride = p->xps;
@@ -472,7 +481,7 @@ cudaError_t enqueue_update_tc(polar_plan_s* p, int k, const StopRule& rule, cuda
     q.st = p->st;
     q.planes_dyn = &p->st->fp8_on;
     if ((e = launch_tc_gemm_fp8(q, s)) != cudaSuccess) return e;
-    p->launches += 2;
+    p->launches += 3;
   }
   TcArgs u{};
   u.M = p->m; u.N = p->n; u.K = p->n;
@@ -853,7 +862,8 @@ polar_status_t polar_gemm_fp8(int transA, int transB, int64_t M, int64_t N, int6
   const int64_t kp = round_up(K, 16), kb = (K + 127) / 128;
   const int64_t mb = (M + 127) / 128, nb = (N + 127) / 128;
   const size_t oa = 0, ob = round_up(M * kp, 256), oea = ob + round_up(N * kp, 256), oeb = oea + round_up(mb * kb, 256);
-  const size_t bytes = oeb + round_up(nb * kb, 256);
+  const size_t oua = oeb + round_up(nb * kb, 256), oub = oua + round_up(mb, 256);
+  const size_t bytes = oub + round_up(nb, 256);
   void* scr = nullptr;
   polar_status_t r = scratch_get(bytes, &scr);
   if (r != POLAR_OK) return r;
@@ -862,10 +872,12 @@ polar_status_t polar_gemm_fp8(int transA, int transB, int64_t M, int64_t N, int6
   uint8_t* cb = w + ob;
   int8_t* ea = (int8_t*)(w + oea);
   int8_t* eb = (int8_t*)(w + oeb);
+  uint8_t* ua = w + oua;
+  uint8_t* ub = w + oub;
   // op(A) = A (stored M x K) or A^T (stored K x M: transposed into M x K); op(B)^T = B^T (B stored K x N:
   // transposed into N x K) or B (stored N x K)
-  CK(launch_quantize_codes(A, false, lda, 0, a_rows, a_cols, ca, kp, ea, kb, transA != 0, nullptr, s));
-  CK(launch_quantize_codes(B, false, ldb, 0, b_rows, b_cols, cb, kp, eb, kb, transB == 0, nullptr, s));
+  CK(launch_quantize_codes(A, false, lda, 0, a_rows, a_cols, ca, kp, ea, kb, transA != 0, ua, nullptr, s));
+  CK(launch_quantize_codes(B, false, ldb, 0, b_rows, b_cols, cb, kp, eb, kb, transB == 0, ub, nullptr, s));
   TcArgs g{};
   g.M = M; g.N = N; g.K = K;
   g.a = op_planes((const uint16_t*)ca, M, K, kp, 0, 1);
@@ -875,6 +887,7 @@ polar_status_t polar_gemm_fp8(int transA, int transB, int64_t M, int64_t N, int6
   g.C = C; g.ldc = ldc; g.alpha = alpha; g.beta = beta;
   g.a_exp = ea; g.lde_a = kb;
   g.b_exp = eb; g.lde_b = kb;
+  g.a_uni = ua; g.b_uni = ub;
   return launch_tc_gemm_fp8(g, s) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 

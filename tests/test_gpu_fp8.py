@@ -172,3 +172,23 @@ def test_gemm_fp8_identity_gives_the_oracles_codes(lib, trans, shape):
     C = torch.full((m, k), np.nan, dtype=torch.float32, device="cuda")
     lib.polar_gemm_fp8(torch.eye(m, device="cuda"), X, C, False, trans)
     assert np.array_equal(to_np(C), want)
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
+def test_gemm_fp8_one_scale_tiles_accumulate_runs(lib, ta, tb):
+    """Standard normal operands: every 128 x 128 tile's maximum lies in (3.5, 7], so every tile has
+    the same exponent and whole tiles accumulate several K blocks under one scale (here 17 blocks:
+    runs of 8, 8 and a ragged 1). The product stays within float32 accumulation of the oracle's
+    quantized operands."""
+    import torch
+    m, n, k = 300, 260, 2100
+    rng = np.random.default_rng(77 + ta)
+    a, b, oa, ob = _ops(rng, m, n, k, ta, tb, lambda r, s: r.standard_normal(s).astype(np.float32))
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    lib.polar_gemm_fp8(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), C, ta, tb)
+    qa = quantize_tiles_e4m3(np.ascontiguousarray(oa)).astype(np.float64)
+    qb = quantize_tiles_e4m3(np.ascontiguousarray(ob)).astype(np.float64)
+    want = qa @ qb
+    bound = (k + 4) * 2.0 ** -20 * (np.abs(qa) @ np.abs(qb)) + 1e-30
+    err = np.abs(to_np(C).astype(np.float64) - want)
+    assert np.all(err <= bound), float(np.max(err / bound))
