@@ -170,3 +170,25 @@ def test_new_entry_points_check_arguments_without_gpu(built_lib):
                                       polar.POLAR_AUTO, None) == polar.POLAR_EINVAL   # null C first
     with pytest.raises(ValueError):
         polar.polar_run_host(None, torch.zeros(4, 3, dtype=torch.float64), torch.zeros(4, 3), torch.zeros(3, 3))
+
+
+def test_fp8_product_checks_arguments_without_gpu(built_lib):
+    """polar_gemm_fp8 rejects bad sizes, a null C, null operands and short leading dimensions on the
+    host, treats an empty output as a no-op, and reports the missing device for a valid call."""
+    torch = pytest.importorskip("torch")
+    from paper_2112_09017_gb300 import polar
+    lib = polar.load()
+    f = lib.polar_gemm_fp8
+    dummy = ctypes.c_void_p(16)    # never dereferenced: every case returns before any device work
+    assert f(0, 0, -1, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 4, None) == polar.POLAR_EINVAL
+    assert f(0, 0, 4, 4, -1, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 4, None) == polar.POLAR_EINVAL
+    assert f(0, 0, 0, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 4, None) == polar.POLAR_OK      # M = 0
+    assert f(0, 0, 4, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, None, 4, None) == polar.POLAR_EINVAL   # null C
+    assert f(0, 0, 4, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 3, None) == polar.POLAR_EINVAL  # ldc < N
+    assert f(0, 0, 4, 4, 4, 1.0, None, 4, dummy, 4, 0.0, dummy, 4, None) == polar.POLAR_EINVAL   # null A
+    assert f(0, 0, 4, 5, 6, 1.0, dummy, 5, dummy, 5, 0.0, dummy, 5, None) == polar.POLAR_EINVAL  # lda < K
+    assert f(1, 0, 4, 5, 6, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 5, None) == polar.POLAR_EINVAL  # ldb < N
+    if not torch.cuda.is_available():
+        assert f(0, 0, 4, 5, 6, 1.0, dummy, 6, dummy, 5, 0.0, dummy, 5, None) == polar.POLAR_ECUDA
+    with pytest.raises(ValueError):
+        polar.polar_gemm_fp8(torch.zeros(4, 3), torch.zeros(3, 2), torch.zeros(4, 2))   # host tensors
