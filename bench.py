@@ -316,7 +316,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "m": w.m, "n": w.n, "kappa": w.kappa, "tol": w.tol},
+            "config": workload_config(w, args.prec, world),
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -451,6 +451,18 @@ def accuracy_sampled(torch, A, U, H, k=512, seed=0):
     R = A[:, S].double() - U64 @ H[:, S].double()
     bwd = math.sqrt(R.square().sum().item() / k * n) / torch.linalg.matrix_norm(A.double()).item()
     return {"orth": orth, "bwd": bwd, "sampled_columns": k}
+
+
+def workload_config(w, prec, world):
+    """The `config` of both arms' JSON lines: the workload and the settings it is run with."""
+    big = w.m * w.n > 8192 * 8192
+    return {"workload": w.name, "m": w.m, "n": w.n, "kappa": w.kappa, "tol": w.tol, "precision": prec,
+            "l2": (f"inputs larger than L2 (A is {w.m * w.n * 4 / 2**20:.0f} MiB; L2 129 MB)"
+                   if w.m * w.n * 4 > 129e6 else
+                   f"inputs smaller than L2, not flushed between steps (A is {w.m * w.n * 4 / 2**20:.1f} MiB)"),
+            "parallelism": "independent replicas" if world > 1 else "single GPU",
+            "input": "drawn on the device: float32 QR factors, float64 product" if big else
+                     "host recipe (numpy float64)"}
 
 
 def compact(x, digits=4):
@@ -643,11 +655,7 @@ def run_ours(args):
                                            "accumulate", "bf16": "bf16, f32 accumulate", "fp32": "f32"}.get(
                 args.prec, args.prec),
             "data": "synthetic",
-            "config": {"workload": w.name, "m": m, "n": n, "kappa": w.kappa, "tol": w.tol, "precision": args.prec,
-                       "l2": f"inputs larger than L2 (A is {m * n * 4 / 2**20:.0f} MiB; L2 129 MB)",
-                       "parallelism": "independent replicas" if world > 1 else "single GPU",
-                       "input": "drawn on the device: float32 QR factors, float64 product" if big else
-                                "host recipe (numpy float64)"},
+            "config": workload_config(w, args.prec, world),
             "gpu_launches": launches, "solves_per_s": solves_per_s, "iters": iters,
             "paper_convention_tflops": value * (4.0 * iters) / (3 * iters + 3), "accuracy": acc,
             "kernel_ms": {"gram": ms_gram / max(n_gram, 1), "update": ms_upd / max(n_upd, 1)},

@@ -72,3 +72,14 @@ def test_kernel_source_hash_is_sixteen_hex_digits(bench_mod):
 def test_compact_rounds_floats_only(bench_mod):
     d = bench_mod.compact({"a": 1234.5678, "b": [0.000123456, 7], "c": "x", "d": float("nan"), "e": True})
     assert d == {"a": 1235.0, "b": [0.0001235, 7], "c": "x", "d": None, "e": True}
+
+
+def test_both_arms_share_the_config(bench_mod):
+    """The reference arm's line names the same config as the GPU arm's: one builder serves both."""
+    from paper_2112_09017_gb300 import synth
+    r = _run(["--impl", "reference", "--workload", "square512_k1e2", "--steps", "1", "--warmup", "0"])
+    assert r.returncode == 0, r.stderr
+    got = json.loads(r.stdout.strip().splitlines()[-1])["config"]
+    assert got == bench_mod.workload_config(synth.WORKLOADS["square512_k1e2"], "bf16x6", 1)
+    big = bench_mod.workload_config(synth.WORKLOADS["square32768_k1e8"], "bf16x6", 1)
+    assert big["l2"].startswith("inputs larger than L2") and big["input"].startswith("drawn on the device")
