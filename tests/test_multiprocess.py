@@ -73,6 +73,7 @@ def test_reference_arm_json_line(monkeypatch, capsys):
 
     class A:
         workload = "square512_k1e2"
+        prec = "bf16x6"
         steps = 2
         warmup = 1
     assert bench.run_reference(A()) == 0
