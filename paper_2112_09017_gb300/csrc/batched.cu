@@ -29,7 +29,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kStored = 3;       // BF16 planes kept for X and G
 constexpr int kEpiWarps = 8;     // residual partials per Gram tile (one per epilogue warp)
-constexpr int kBM = 128, kBN = 256;
+constexpr int kBM = 128;         // tile rows (the tile width is per problem)
 
 int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
